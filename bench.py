@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Splotch frame render (particles/s per GB300).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+A step is one frame of the whole hot path -- rasterise, bin, tile pass, large
+pass -- over the workload's particle set, which is resident in HBM before the
+timed region starts.  `value` is particles rendered per second over all
+ranks; `e2e` is the same metric through the C ABI with host buffers (particle
+upload and image download inside the timed region).  Under torchrun every
+rank renders its own copy of the workload (independent frames, weak scaling,
+no collective on the data path); timing is the max over ranks.
+
+`--impl reference` times the FP64 CPU oracle (the correctness reference) on
+the host cores, each step a random sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "clustered": {"scene": "clustered", "label": "clustered-10M-1024sq-f32",
+                  "desc": "10M particles, 70% in 500 Plummer haloes + 30% uniform background, "
+                          "density-derived h, FP32 attributes, 1024x1024 RGB FP32"},
+    "precision": {"scene": "precision", "label": "clustered-100M-2048sq-f16attr", "fp16": True,
+                  "desc": "100M clustered particles, h/I/s stored FP16, 2048x2048 RGB FP32"},
+    "precision32": {"scene": "precision", "label": "clustered-100M-2048sq-f32",
+                    "desc": "100M clustered particles, FP32 attributes, 2048x2048 RGB FP32"},
+    "uniform": {"scene": "uniform", "label": "uniform-200k-256sq-f32",
+                "desc": "200k uniform particles, log-normal h, 256x256 RGB FP32"},
+}
+METRIC = "particles/s per GB300 at stated error vs FP64 oracle; % of HBM roofline"
+FLOPS_PER_PAIR = 7      # separable weight product (1 mul) + 3 multiply-adds
+FLOPS_PER_POINT = 3     # 3 adds
+FP32_LANES_PER_SM = 128
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1309_1114_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, label: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(f"{kernel}@{label}")
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def oracle_sample_rate(scene, cam, target_s: float, seed: int = 0):
+    """Time the FP64 oracle (all host cores) on a random sample of the scene,
+    sized to take about target_s seconds.  Returns (particles/s, sample, cores, secs)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    m = min(scene.n, 20000)
+    for _ in range(4):
+        idx = np.sort(rng.choice(scene.n, m, replace=False))
+        sub = {k: v[idx] for k, v in scene.parts.items()}
+        t0 = time.perf_counter()
+        oracle.render(sub, scene.palette, cam, {}, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or m == scene.n:
+            return m / dt, m, cores, dt
+        m = int(min(scene.n, max(m * 2, m * target_s / max(dt, 1e-3))))
+    return m / dt, m, cores, dt
+
+
+def make_scene(wl: dict):
+    from paper_1309_1114_gb300 import scenes
+    return scenes.make(wl["scene"])
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    scene = make_scene(wl)
+    cam = scene.cams[0]
+    # size one step to ~2 s of oracle work on all cores
+    rate, m, cores, _ = oracle_sample_rate(scene, cam, 2.0)
+    import oracle
+    rng = np.random.default_rng(1)
+    times = []
+    for k in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(scene.n, m, replace=False))
+        sub = {kk: v[idx] for kk, v in scene.parts.items()}
+        t0 = time.perf_counter()
+        oracle.render(sub, scene.palette, cam, {}, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    value = m / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["label"], "description": wl["desc"],
+                   "n_particles": scene.n, "image": [cam["width"], cam["height"]]},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{m} particles drawn at random per step from the "
+                                   f"{scene.n}-particle workload, full {cam['width']}x"
+                                   f"{cam['height']} image, FP64, OpenMP over {cores} threads"},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, wl):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1309_1114_gb300.splotch import Renderer
+
+    scene = make_scene(wl)
+    cam = scene.cams[0]
+    W, H = cam["width"], cam["height"]
+    fp16 = scene.fp16 if wl.get("fp16") else None
+    stream = torch.cuda.current_stream()
+    r = Renderer(local, stream.cuda_stream)
+    r.load(scene.parts, fp16)
+    r.set_colormap(scene.palette)
+    r.set_camera(cam)
+    r.set_params()
+    img = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
+    work = r.count_work()
+
+    for _ in range(args.warmup):
+        r.render(img)
+    torch.cuda.synchronize()
+    r.set_timing(True)
+    sampler = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r.render(img)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = r.stats()
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * scene.n / (ms * 1e-3)
+
+    # per-stage device times over the timed frames (CUDA events on the render stream)
+    nfr = max(st["timed_frames"], 1)
+    stage = dict(zip(["raster", "bin", "tile", "large", "epilogue", "total"],
+                     [v / nfr for v in st["sum_ms"]]))
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12    # TFLOP/s
+    tile_flops = FLOPS_PER_POINT * work[0] + FLOPS_PER_PAIR * (work[1] + work[2])
+    large_flops = FLOPS_PER_PAIR * work[3]
+    dom = "tile" if stage["tile"] >= stage["large"] else "large"
+    flops = tile_flops if dom == "tile" else large_flops
+    achieved = flops / (stage[dom] * 1e-3) / 1e12 if stage[dom] > 0 else 0.0
+    kname = "tile_kernel" if dom == "tile" else "tile_kernel_large"
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
+                "kernel": kname, "kernel_ms": stage[dom],
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                              f"{sm_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+                "work": {"point_deposits": work[0], "small_pairs": work[1],
+                         "medium_pairs": work[2], "large_pairs": work[3],
+                         "flops_per_pair": FLOPS_PER_PAIR}}
+    bytes_per_particle = 18 if fp16 is not None else 24
+    alg_bytes = scene.n * bytes_per_particle + 12 * W * H
+    hbm = float(peaks.get("hbm_gbs", 6771.1))
+    hbm_frac = alg_bytes / (ms * 1e-3) / (hbm * 1e9)
+
+    # end to end through the C ABI with host buffers (upload + render + download)
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+           for k, v in (dict(scene.parts, **fp16) if fp16 is not None else scene.parts).items()}
+    host_parts = {k: v.numpy() for k, v in pin.items()}
+    host_img = torch.empty((H, W, 3), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    r.set_timing(False)
+    if ws > 1:
+        torch.distributed.barrier()
+    xyz = {k: host_parts[k] for k in ("x", "y", "z")}
+    attrs = {k: host_parts[k] for k in ("h", "I", "s")}
+    host_np = host_img.numpy()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        if fp16 is None:
+            r.load(dict(xyz, **attrs))
+        else:
+            r.load(xyz, attrs)
+        r.render_host(host_np)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * scene.n / e2e_s, "unit": "particles/s",
+           "h2d_bytes_per_step": scene.n * bytes_per_particle, "d2h_bytes_per_step": 12 * W * H,
+           "ms_per_step": 1e3 * e2e_s}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, m, cores, secs = oracle_sample_rate(scene, cam, 10.0)
+        cpu = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
+               "sample": f"{m} particles drawn at random from the workload, full {W}x{H} image, "
+                         f"FP64, OpenMP over {cores} threads, {secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["label"], "description": wl["desc"],
+                       "n_particles": scene.n, "image": [W, H],
+                       "attributes": "f16" if fp16 is not None else "f32",
+                       "tile_px": 32, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (particles + per-frame records > 129 MB); no flush"},
+            "roofline": roofline,
+            "hbm_roofline_frac": hbm_frac,
+            "hbm_alg_bytes_per_step": alg_bytes,
+            "stage_ms": stage,
+            "stats": {k: st[k] for k in ("n_active", "n_point", "n_small", "n_medium", "n_large")}
+            | {"n_entries": st["n_entries"], "n_tiles": st["n_tiles"]},
+            "e2e": e2e,
+            "gpu_launches": int(st["launches"]) * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    r.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="clustered")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

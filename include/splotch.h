@@ -1,0 +1,184 @@
+/*
+ * splotch.h -- C ABI of the GB300 (sm_103a) Splotch frame renderer.
+ *
+ * The library renders one frame of a particle set the way Sec. 2 of
+ * "GPU Accelerated Particle Visualization with Splotch" (Rivi et al.)
+ * describes it: rasterisation (normalisation, roto-translation and
+ * perspective projection, colour look-up, activity test) followed by the
+ * rendering of every active particle as the clipped Gaussian of Eq. 2,
+ * accumulated additively (Eq. 1 with E_p = A_p, so the order of particles
+ * does not matter).  Particles are classified by their screen radius
+ * (Eq. 7) as in Sec. 4: point-like (r <= r_sml), tile-resident and large.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: SPL_OK (0) or one of the SPL_E*
+ *     codes below; spl_error_string() names it.  No C++ exception crosses
+ *     the boundary.
+ *   - Invalid arguments return SPL_EINVAL and change nothing.  Allocation
+ *     failure returns SPL_ENOMEM.  A CUDA error raised by an earlier,
+ *     asynchronous launch is returned by the next call that synchronises
+ *     (SPL_ECUDA); a device-side check that failed (a list overflow or an
+ *     index guard) is returned as SPL_EDEVICE by the next render call (the
+ *     flag is then cleared).
+ *   - One context belongs to one device and one CUDA stream; it is not
+ *     thread-safe.  All device work of a call is issued on the context's
+ *     stream unless the call takes a stream argument, in which case that
+ *     stream is used.  NULL means the legacy default stream.
+ *   - Pointers marked "device" must be device memory of the context's
+ *     device (for example a torch CUDA tensor's data_ptr()); pointers marked
+ *     "host" are ordinary (preferably pinned) host memory.
+ *   - The library owns the particle storage and all scratch memory; the
+ *     caller owns images and every buffer it passes in.
+ *   - Images are row-major, y downwards, RGB interleaved, FP32:
+ *     pixel (i, j) channel c lives at index 3 * (j * width + i) + c.
+ */
+#ifndef SPLOTCH_H
+#define SPLOTCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SPL_OK 0
+#define SPL_EINVAL 1    /* invalid argument */
+#define SPL_ENOMEM 2    /* device or host allocation failed */
+#define SPL_ECUDA 3     /* CUDA runtime error */
+#define SPL_ESTATE 4    /* call out of order (e.g. render before particles) */
+#define SPL_EDEVICE 5   /* a device-side check failed during the last render */
+
+/* memory space of caller buffers */
+#define SPL_MEM_HOST 0
+#define SPL_MEM_DEVICE 1
+
+/* storage type of the per-particle attributes h, I, s */
+#define SPL_ATTR_F32 0
+#define SPL_ATTR_F16 1   /* IEEE binary16; widened to FP32 on load (Sec. 3.2.3 ideal of
+                            one load per particle, half the attribute bytes) */
+
+/* output modes */
+#define SPL_MODE_ADDITIVE 0   /* image = sum of clipped Gaussians (Eq. 1, E_p = A_p, thin) */
+#define SPL_MODE_EA 1         /* image = 1 - exp(-sum), the E_p = A_p solution of Eq. 1 */
+
+/* tile schedulers */
+#define SPL_SCHED_NONE 0      /* tiles in image order */
+#define SPL_SCHED_COUNT 1     /* longest-first by the count heuristic */
+#define SPL_SCHED_MLP 2       /* longest-first by the tile-cost network */
+
+typedef struct spl_ctx spl_ctx;
+
+/* Particle set (Sec. 2 "Data Loading": at least three coordinates, plus the
+ * smoothing length, an intensity and a colour scalar).  n may be 0. */
+typedef struct {
+    int64_t n;
+    const float *x, *y, *z;    /* positions, FP32, n each */
+    const void *h, *I, *s;     /* smoothing length, intensity, colour scalar:
+                                  float or binary16 according to attr_type */
+    int32_t attr_type;         /* SPL_ATTR_F32 or SPL_ATTR_F16 */
+    int32_t mem_space;         /* SPL_MEM_HOST or SPL_MEM_DEVICE (all six) */
+} spl_particles;
+
+/* Pinhole camera (Sec. 2 "roto-translated and projected according to camera
+ * settings").  Basis: fwd = unit(target - eye), right = unit(fwd x up),
+ * up' = right x fwd; focal length f = (height/2) / tan(fov_y/2);
+ * x_s = width/2 + f x_c / z_c, y_s = height/2 - f y_c / z_c; pixel (i, j)
+ * has its centre at (i + 1/2, j + 1/2).  Particles with z_c <= z_near are
+ * inactive. */
+typedef struct {
+    double eye[3], target[3], up[3];
+    double fov_y_deg;          /* in (0, 180) */
+    int32_t width, height;     /* 1 .. 16384 */
+    double z_near;             /* > 0 */
+} spl_camera;
+
+/* Render parameters.  Eq. 2: rho = rho0 exp(-d^2/sigma^2), clipped beyond
+ * chi*sigma; sigma = sigma_per_h * h; Eq. 7: r = chi * sigma * f / (z_c s_box).
+ * r_sml is the point-rule radius of Sec. 4; r_small and r_large only choose
+ * how a particle is processed (they never change the image). */
+typedef struct {
+    double chi;                /* clip factor (default 3) */
+    double sigma_per_h;        /* default 1 */
+    double s_box;              /* S_box of Eq. 7 (default 1) */
+    double r_sml;              /* point rule for r <= r_sml (default 0.5) */
+    double brightness;         /* emission scale (default 1) */
+    int32_t tile_px;           /* tile side t_x = t_y of Eq. 8: 16 or 32 (default 32) */
+    double r_small;            /* r_sml < r <= r_small: one thread per particle (default 4) */
+    double r_large;            /* r > r_large: large pass (default 64) */
+    int32_t mode;              /* SPL_MODE_ADDITIVE or SPL_MODE_EA */
+    int32_t sched;             /* SPL_SCHED_* (default SPL_SCHED_NONE) */
+} spl_params;
+
+/* Per-frame statistics of the last render (counts are exact).  With timing
+ * enabled (spl_set_timing) every render records CUDA events between its
+ * stages on the render stream; the ms_* fields are the last frame's stage
+ * times and sum_ms[] / timed_frames accumulate them (order: raster, bin,
+ * tile, large, epilogue, total) since timing was last enabled.  Reading the
+ * stats waits for the last frame to finish. */
+typedef struct {
+    int64_t n_particles, n_active, n_point, n_small, n_medium, n_large;
+    int64_t n_entries[4];      /* tile-list entries: point, small, medium, large */
+    int32_t n_tiles, tile_px;
+    float ms_raster, ms_bin, ms_tile, ms_large, ms_epilogue, ms_total;
+    int64_t timed_frames;
+    double sum_ms[6];
+    int32_t launches;          /* kernels the last render launched */
+} spl_stats;
+
+/* Context lifecycle.  device: CUDA ordinal; stream: cudaStream_t or NULL. */
+int spl_create(spl_ctx **out, int device, void *stream);
+int spl_destroy(spl_ctx *ctx);     /* NULL is accepted and ignored */
+
+/* Copy a particle set into the library's device SoA storage (replacing any
+ * earlier set).  Host sources are copied with cudaMemcpyAsync on the
+ * context stream; the call returns after the copy has completed. */
+int spl_load_particles(spl_ctx *ctx, const spl_particles *p);
+
+/* Camera, colour map and parameters.  The colour map is n >= 1 RGB FP32
+ * triples (host memory), looked up by s' = clamp((s - s_min)/(s_max - s_min),
+ * 0, 1) with linear interpolation between the n entries (Sec. 2 palettes). */
+int spl_set_camera(spl_ctx *ctx, const spl_camera *cam);
+int spl_set_colormap(spl_ctx *ctx, const float *rgb, int32_t n, float s_min, float s_max);  /* 1 <= n <= 1024 */
+int spl_default_params(spl_params *out);
+int spl_set_params(spl_ctx *ctx, const spl_params *q);
+int spl_get_params(spl_ctx *ctx, spl_params *out);
+
+/* Render the loaded particles with the current camera into d_image (device,
+ * width*height*3 FP32, caller-owned, fully overwritten).  stream: NULL means
+ * the context stream.  The call synchronises once after binning (to size the
+ * tile lists) and returns with the remaining kernels queued on the stream. */
+int spl_render(spl_ctx *ctx, float *d_image, void *stream);
+
+/* Same, into host memory: renders into library scratch and copies the image
+ * to h_image (width*height*3 floats); returns when the copy has completed. */
+int spl_render_host(spl_ctx *ctx, float *h_image);
+
+/* Render n_views cameras of the same particle set; d_images[k] (device) holds
+ * cams[k].width * cams[k].height * 3 floats.  All views are binned first and
+ * rendered by one persistent launch over every (view, tile) work item. */
+int spl_render_batch(spl_ctx *ctx, const spl_camera *cams, int32_t n_views,
+                     float *const *d_images, void *stream);
+
+int spl_get_stats(spl_ctx *ctx, spl_stats *out);
+int spl_set_timing(spl_ctx *ctx, int32_t enable);   /* per-stage CUDA events; resets sums */
+
+/* Work of the current camera and particle set, counted exactly by a separate
+ * diagnostic kernel (not part of a render): out[0] = point deposits that land
+ * on the image, out[1..3] = covered (particle, pixel) pairs, d^2 <= r^2, of
+ * the small, medium and large classes.  Used for roofline accounting. */
+int spl_count_work(spl_ctx *ctx, int64_t out[4]);
+
+/* Diagnostics used by the tests.  spl_get_records copies the last render's
+ * per-particle rasterisation results for particles [0, n) into host arrays
+ * (any may be NULL): screen position x_s, y_s (as double), screen radius r,
+ * emission e (n*3), class (-2 inactive, 0 point, 1 small, 2 medium, 3 large). */
+int spl_get_records(spl_ctx *ctx, int64_t n, double *xs, double *ys, float *r,
+                    float *e, int32_t *cls);
+
+const char *spl_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLOTCH_H */

@@ -1,0 +1,584 @@
+// spl_api.cu -- the C ABI (include/splotch.h): context, particle storage,
+// camera / colour map / parameters, and the per-frame pipeline
+//   raster+count -> count large -> scan -> [sync: size lists] -> scatter ->
+//   tile pass -> large pass -> (E=A epilogue)
+// all on one stream.
+#include <cmath>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <new>
+
+#include "splotch.h"
+#include "spl_internal.cuh"
+
+using namespace spl;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;   // elements
+    int ensure(size_t n) {
+        if (n <= cap && p) return SPL_OK;
+        size_t want = n < 16 ? 16 : n + n / 4;
+        T *q = nullptr;
+        if (cudaMalloc((void **)&q, want * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            return SPL_ENOMEM;
+        }
+        if (p) cudaFree(p);
+        p = q;
+        cap = want;
+        return SPL_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct spl_ctx {
+    int device = 0;
+    int sms = 1;
+    cudaStream_t stream = nullptr;
+    // particles (SoA)
+    int64_t n = 0;
+    int attr_type = SPL_ATTR_F32;
+    bool have_particles = false;
+    DevBuf<float> x, y, z;
+    DevBuf<unsigned char> h, I, s;
+    // colour map
+    DevBuf<float> pal;
+    int npal = 0;
+    float s_min = 0.f, s_max = 1.f;
+    // camera and parameters
+    spl_camera cam{};
+    bool have_cam = false;
+    spl_params par{};
+    // scratch
+    DevBuf<float4> rec0, rec1;
+    DevBuf<int> counts, offsets, cursor;
+    DevBuf<unsigned> large_ids, entries;
+    DevBuf<DevStats> dstats;
+    DevBuf<float> host_img_scratch;
+    DevStats *hstats = nullptr;   // pinned
+    // timing: two event sets, so that a frame's stage times are read at the
+    // next frame's synchronisation point without an extra wait
+    bool timing = false;
+    cudaEvent_t ev[2][6] = {};
+    int ev_set = 0;
+    bool ev_pending[2] = {false, false};
+    double sum_ms[6] = {};
+    int64_t timed_frames = 0;
+    float last_ms[6] = {};
+    spl_stats last{};
+};
+
+static int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SPL_OK;
+    if (e == cudaErrorMemoryAllocation) return SPL_ENOMEM;
+    return SPL_ECUDA;
+}
+
+#define SPL_TRY(expr)                      \
+    do {                                   \
+        int _rc = (expr);                  \
+        if (_rc != SPL_OK) return _rc;     \
+    } while (0)
+#define SPL_CUDA(expr) SPL_TRY(cuda_status(expr))
+
+extern "C" const char *spl_error_string(int code) {
+    switch (code) {
+        case SPL_OK: return "ok";
+        case SPL_EINVAL: return "invalid argument";
+        case SPL_ENOMEM: return "out of memory";
+        case SPL_ECUDA: return "CUDA error";
+        case SPL_ESTATE: return "call out of order";
+        case SPL_EDEVICE: return "device-side check failed";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int spl_default_params(spl_params *q) {
+    if (!q) return SPL_EINVAL;
+    q->chi = 3.0;
+    q->sigma_per_h = 1.0;
+    q->s_box = 1.0;
+    q->r_sml = 0.5;
+    q->brightness = 1.0;
+    q->tile_px = 32;
+    q->r_small = 4.0;
+    q->r_large = 64.0;
+    q->mode = SPL_MODE_ADDITIVE;
+    q->sched = SPL_SCHED_NONE;
+    return SPL_OK;
+}
+
+static bool params_ok(const spl_params *q) {
+    return q && std::isfinite(q->chi) && q->chi > 0 && std::isfinite(q->sigma_per_h) &&
+           q->sigma_per_h > 0 && std::isfinite(q->s_box) && q->s_box > 0 &&
+           std::isfinite(q->r_sml) && q->r_sml >= 0 && std::isfinite(q->brightness) &&
+           (q->tile_px == 16 || q->tile_px == 32) && std::isfinite(q->r_small) &&
+           q->r_small >= q->r_sml && std::isfinite(q->r_large) && q->r_large >= q->r_small &&
+           (q->mode == SPL_MODE_ADDITIVE || q->mode == SPL_MODE_EA) && q->sched >= 0 &&
+           q->sched <= SPL_SCHED_MLP;
+}
+
+static bool camera_ok(const spl_camera *c) {
+    if (!c) return false;
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384) return false;
+    if (!(c->fov_y_deg > 0 && c->fov_y_deg < 180) || !(c->z_near > 0)) return false;
+    double f[3], r[3];
+    for (int k = 0; k < 3; ++k) {
+        if (!std::isfinite(c->eye[k]) || !std::isfinite(c->target[k]) || !std::isfinite(c->up[k]))
+            return false;
+        f[k] = c->target[k] - c->eye[k];
+    }
+    r[0] = f[1] * c->up[2] - f[2] * c->up[1];
+    r[1] = f[2] * c->up[0] - f[0] * c->up[2];
+    r[2] = f[0] * c->up[1] - f[1] * c->up[0];
+    return (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) > 0 && (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) > 0;
+}
+
+extern "C" int spl_create(spl_ctx **out, int device, void *stream) {
+    if (!out) return SPL_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return SPL_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return SPL_EINVAL;
+    DeviceGuard g(device);
+    spl_ctx *c = new (std::nothrow) spl_ctx();
+    if (!c) return SPL_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    spl_default_params(&c->par);
+    int rc = c->dstats.ensure(1);
+    if (rc == SPL_OK && cudaMemset(c->dstats.p, 0, sizeof(DevStats)) != cudaSuccess) rc = SPL_ECUDA;
+    if (rc == SPL_OK && cudaMallocHost((void **)&c->hstats, sizeof(DevStats)) != cudaSuccess)
+        rc = SPL_ENOMEM;
+    for (int k = 0; rc == SPL_OK && k < 12; ++k)
+        if (cudaEventCreate(&c->ev[k / 6][k % 6]) != cudaSuccess) rc = SPL_ECUDA;
+    if (rc != SPL_OK) {
+        cudaGetLastError();
+        spl_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return SPL_OK;
+}
+
+extern "C" int spl_destroy(spl_ctx *c) {
+    if (!c) return SPL_OK;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    c->x.release(); c->y.release(); c->z.release();
+    c->h.release(); c->I.release(); c->s.release();
+    c->pal.release();
+    c->rec0.release(); c->rec1.release();
+    c->counts.release(); c->offsets.release(); c->cursor.release();
+    c->large_ids.release(); c->entries.release(); c->dstats.release();
+    c->host_img_scratch.release();
+    if (c->hstats) cudaFreeHost(c->hstats);
+    for (auto &set : c->ev)
+        for (auto &e : set)
+            if (e) cudaEventDestroy(e);
+    delete c;
+    return SPL_OK;
+}
+
+extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
+    if (!c || !p || p->n < 0) return SPL_EINVAL;
+    if (p->attr_type != SPL_ATTR_F32 && p->attr_type != SPL_ATTR_F16) return SPL_EINVAL;
+    if (p->mem_space != SPL_MEM_HOST && p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
+    if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
+    if (p->n > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // ids are 32-bit
+    DeviceGuard g(c->device);
+    const size_t n = (size_t)p->n;
+    const size_t ab = p->attr_type == SPL_ATTR_F16 ? 2 : 4;
+    SPL_TRY(c->x.ensure(n ? n : 1));
+    SPL_TRY(c->y.ensure(n ? n : 1));
+    SPL_TRY(c->z.ensure(n ? n : 1));
+    SPL_TRY(c->h.ensure((n ? n : 1) * ab));
+    SPL_TRY(c->I.ensure((n ? n : 1) * ab));
+    SPL_TRY(c->s.ensure((n ? n : 1) * ab));
+    const cudaMemcpyKind kind =
+        p->mem_space == SPL_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (n) {
+        SPL_CUDA(cudaMemcpyAsync(c->x.p, p->x, n * 4, kind, c->stream));
+        SPL_CUDA(cudaMemcpyAsync(c->y.p, p->y, n * 4, kind, c->stream));
+        SPL_CUDA(cudaMemcpyAsync(c->z.p, p->z, n * 4, kind, c->stream));
+        SPL_CUDA(cudaMemcpyAsync(c->h.p, p->h, n * ab, kind, c->stream));
+        SPL_CUDA(cudaMemcpyAsync(c->I.p, p->I, n * ab, kind, c->stream));
+        SPL_CUDA(cudaMemcpyAsync(c->s.p, p->s, n * ab, kind, c->stream));
+    }
+    SPL_CUDA(cudaStreamSynchronize(c->stream));
+    c->n = p->n;
+    c->attr_type = p->attr_type;
+    c->have_particles = true;
+    return SPL_OK;
+}
+
+extern "C" int spl_set_camera(spl_ctx *c, const spl_camera *cam) {
+    if (!c || !camera_ok(cam)) return SPL_EINVAL;
+    c->cam = *cam;
+    c->have_cam = true;
+    return SPL_OK;
+}
+
+extern "C" int spl_set_colormap(spl_ctx *c, const float *rgb, int32_t n, float s_min, float s_max) {
+    if (!c || !rgb || n < 1 || n > kMaxPalette) return SPL_EINVAL;
+    if (!std::isfinite(s_min) || !std::isfinite(s_max)) return SPL_EINVAL;
+    for (int k = 0; k < 3 * n; ++k)
+        if (!std::isfinite(rgb[k])) return SPL_EINVAL;
+    DeviceGuard g(c->device);
+    SPL_TRY(c->pal.ensure((size_t)3 * n));
+    SPL_CUDA(cudaMemcpyAsync(c->pal.p, rgb, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    SPL_CUDA(cudaStreamSynchronize(c->stream));
+    c->npal = n;
+    c->s_min = s_min;
+    c->s_max = s_max;
+    return SPL_OK;
+}
+
+extern "C" int spl_set_params(spl_ctx *c, const spl_params *q) {
+    if (!c || !params_ok(q)) return SPL_EINVAL;
+    c->par = *q;
+    return SPL_OK;
+}
+
+extern "C" int spl_get_params(spl_ctx *c, spl_params *out) {
+    if (!c || !out) return SPL_EINVAL;
+    *out = c->par;
+    return SPL_OK;
+}
+
+extern "C" int spl_set_timing(spl_ctx *c, int32_t enable) {
+    if (!c) return SPL_EINVAL;
+    c->timing = enable != 0;
+    c->ev_pending[0] = c->ev_pending[1] = false;
+    for (double &v : c->sum_ms) v = 0.0;
+    c->timed_frames = 0;
+    return SPL_OK;
+}
+
+// Read the stage times of event set k (its last event must have completed).
+static void harvest_timing(spl_ctx *c, int k) {
+    if (!c->ev_pending[k]) return;
+    c->ev_pending[k] = false;
+    for (int st = 0; st < 6; ++st) {
+        const int a = st < 5 ? st : 0, b = st < 5 ? st + 1 : 5;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[k][a], c->ev[k][b]) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        c->last_ms[st] = ms;
+        c->sum_ms[st] += ms;
+    }
+    c->timed_frames += 1;
+}
+
+extern "C" int spl_get_stats(spl_ctx *c, spl_stats *out) {
+    if (!c || !out) return SPL_EINVAL;
+    DeviceGuard g(c->device);
+    for (int q = 0; q < 2; ++q) {
+        const int k = (c->ev_set + q) & 1;   // older set first
+        if (c->ev_pending[k]) {
+            SPL_CUDA(cudaEventSynchronize(c->ev[k][5]));
+            harvest_timing(c, k);
+        }
+    }
+    spl_stats &st = c->last;
+    st.ms_raster = c->last_ms[0];
+    st.ms_bin = c->last_ms[1];
+    st.ms_tile = c->last_ms[2];
+    st.ms_large = c->last_ms[3];
+    st.ms_epilogue = c->last_ms[4];
+    st.ms_total = c->last_ms[5];
+    st.timed_frames = c->timed_frames;
+    for (int k = 0; k < 6; ++k) st.sum_ms[k] = c->sum_ms[k];
+    *out = st;
+    return SPL_OK;
+}
+
+static void split_double(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+// Per-frame constants: the look-at basis and focal length in double, handed
+// to the device as double-float pairs.
+static FrameConst make_frame(const spl_ctx *c, const spl_camera &cam) {
+    FrameConst fc;
+    std::memset(&fc, 0, sizeof(fc));
+    double f[3], r[3], u[3];
+    for (int k = 0; k < 3; ++k) f[k] = cam.target[k] - cam.eye[k];
+    double nf = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (double &v : f) v /= nf;
+    r[0] = f[1] * cam.up[2] - f[2] * cam.up[1];
+    r[1] = f[2] * cam.up[0] - f[0] * cam.up[2];
+    r[2] = f[0] * cam.up[1] - f[1] * cam.up[0];
+    double nr = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (double &v : r) v /= nr;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    const double *rows[3] = {r, u, f};
+    for (int a = 0; a < 3; ++a) {
+        double e = 0;
+        for (int b = 0; b < 3; ++b) {
+            split_double(rows[a][b], fc.Rhi[3 * a + b], fc.Rlo[3 * a + b]);
+            e += rows[a][b] * cam.eye[b];
+        }
+        split_double(e, fc.Ehi[a], fc.Elo[a]);
+    }
+    const double foc = 0.5 * cam.height / std::tan(0.5 * cam.fov_y_deg * M_PI / 180.0);
+    split_double(foc, fc.fhi, fc.flo);
+    fc.half_w = 0.5f * (float)cam.width;
+    fc.half_h = 0.5f * (float)cam.height;
+    fc.z_near = (float)cam.z_near;
+    const spl_params &q = c->par;
+    fc.sig_fac = (float)(q.sigma_per_h / q.s_box);
+    fc.chi = (float)q.chi;
+    fc.r_sml2 = (float)(q.r_sml * q.r_sml);
+    fc.r_small2 = (float)(q.r_small * q.r_small);
+    fc.r_large2 = (float)(q.r_large * q.r_large);
+    fc.s_min = c->s_min;
+    fc.s_inv = c->s_max != c->s_min ? (float)(1.0 / ((double)c->s_max - (double)c->s_min)) : 0.f;
+    fc.brightness = (float)q.brightness;
+    fc.npal = c->npal;
+    fc.width = cam.width;
+    fc.height = cam.height;
+    fc.tile = q.tile_px;
+    fc.ntx = (cam.width + q.tile_px - 1) / q.tile_px;
+    fc.nty = (cam.height + q.tile_px - 1) / q.tile_px;
+    fc.ntiles = fc.ntx * fc.nty;
+    return fc;
+}
+
+static void record_event(spl_ctx *c, int k, cudaStream_t s) {
+    if (c->timing) cudaEventRecord(c->ev[c->ev_set][k], s);
+}
+
+// One frame with camera cam into d_image (device) on stream s.
+static int render_frame(spl_ctx *c, const spl_camera &cam, float *d_image, cudaStream_t s) {
+    if (!c->have_particles || !c->have_cam || c->npal < 1) return SPL_ESTATE;
+    const FrameConst fc = make_frame(c, cam);
+    const size_t n = (size_t)c->n;
+    SPL_TRY(c->rec0.ensure(n ? n : 1));
+    SPL_TRY(c->rec1.ensure(n ? n : 1));
+    SPL_TRY(c->large_ids.ensure(n ? n : 1));
+    SPL_TRY(c->counts.ensure((size_t)NLIST * fc.ntiles));
+    SPL_TRY(c->offsets.ensure((size_t)NLIST * fc.ntiles + 1));
+    SPL_TRY(c->cursor.ensure((size_t)NLIST * fc.ntiles));
+    SPL_TRY(c->entries.ensure(16));
+    SPL_CUDA(cudaGetLastError());
+
+    record_event(c, 0, s);
+    SPL_CUDA(cudaMemsetAsync(c->counts.p, 0, sizeof(int) * NLIST * fc.ntiles, s));
+    SPL_CUDA(cudaMemsetAsync(c->dstats.p, 0, offsetof(DevStats, err), s));
+    RasterArgs ra{};
+    ra.n = c->n;
+    ra.x = c->x.p; ra.y = c->y.p; ra.z = c->z.p;
+    ra.h = c->h.p; ra.I = c->I.p; ra.s = c->s.p;
+    ra.pal = c->pal.p;
+    ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
+    ra.counts = c->counts.p;
+    ra.large_ids = c->large_ids.p;
+    ra.st = c->dstats.p;
+    launch_raster(fc, ra, c->attr_type == SPL_ATTR_F16, c->sms, s);
+    record_event(c, 1, s);
+    BinArgs ba{};
+    ba.n = c->n;
+    ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
+    ba.large_ids = c->large_ids.p;
+    ba.counts = c->counts.p;
+    ba.cursor = c->cursor.p;
+    ba.st = c->dstats.p;
+    launch_count_large(fc, ba, c->sms, s);
+    launch_scan(fc, c->counts.p, c->offsets.p, c->cursor.p, c->dstats.p, s);
+    SPL_CUDA(cudaGetLastError());
+    SPL_CUDA(cudaMemcpyAsync(c->hstats, c->dstats.p, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    SPL_CUDA(cudaStreamSynchronize(s));
+    harvest_timing(c, c->ev_set ^ 1);   // the previous frame has finished
+    if (c->hstats->err) {
+        // a device-side check failed in this or an earlier frame
+        SPL_CUDA(cudaMemsetAsync(&c->dstats.p->err, 0, sizeof(unsigned), s));
+        return SPL_EDEVICE;
+    }
+    int64_t total = 0;
+    for (int k = 0; k < NLIST; ++k) total += c->hstats->totals[k];
+    if (total > (int64_t)0x7FFFFFFF) return SPL_ENOMEM;   // list positions are int32
+    SPL_TRY(c->entries.ensure((size_t)(total ? total : 1)));
+    ba.entries = c->entries.p;
+    ba.entries_cap = (int64_t)c->entries.cap;
+    launch_scatter(fc, ba, c->sms, s);
+    record_event(c, 2, s);
+    TileArgs ta{};
+    ta.rec0 = c->rec0.p; ta.rec1 = c->rec1.p;
+    ta.offsets = c->offsets.p;
+    ta.entries = c->entries.p;
+    ta.image = d_image;
+    ta.st = c->dstats.p;
+    launch_tile_pass(fc, ta, s);
+    record_event(c, 3, s);
+    if (c->hstats->totals[L_LARGE] > 0) launch_large_pass(fc, ta, s);
+    record_event(c, 4, s);
+    if (c->par.mode == SPL_MODE_EA)
+        launch_epilogue_ea(d_image, (int64_t)3 * cam.width * cam.height, c->sms, s);
+    record_event(c, 5, s);
+    SPL_CUDA(cudaGetLastError());
+
+    int launches = 2 + (c->n > 0 ? 4 : 0);
+    if (c->hstats->totals[L_LARGE] > 0) launches += 1;
+    if (c->par.mode == SPL_MODE_EA) launches += 1;
+    if (c->timing) {
+        c->ev_pending[c->ev_set] = true;
+        c->ev_set ^= 1;
+    }
+    spl_stats &st = c->last;
+    std::memset(&st, 0, sizeof(st));
+    st.launches = launches;
+    st.n_particles = c->n;
+    st.n_active = (int64_t)c->hstats->n_active;
+    st.n_point = (int64_t)c->hstats->n_point;
+    st.n_small = (int64_t)c->hstats->n_small;
+    st.n_medium = (int64_t)c->hstats->n_medium;
+    st.n_large = (int64_t)c->hstats->n_large;
+    for (int k = 0; k < NLIST; ++k) st.n_entries[k] = c->hstats->totals[k];
+    st.n_tiles = fc.ntiles;
+    st.tile_px = fc.tile;
+    return SPL_OK;
+}
+
+extern "C" int spl_render(spl_ctx *c, float *d_image, void *stream) {
+    if (!c || !d_image) return SPL_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    return render_frame(c, c->cam, d_image, s);
+}
+
+extern "C" int spl_render_host(spl_ctx *c, float *h_image) {
+    if (!c || !h_image) return SPL_EINVAL;
+    if (!c->have_cam) return SPL_ESTATE;
+    DeviceGuard g(c->device);
+    const size_t nv = (size_t)3 * c->cam.width * c->cam.height;
+    SPL_TRY(c->host_img_scratch.ensure(nv));
+    SPL_TRY(render_frame(c, c->cam, c->host_img_scratch.p, c->stream));
+    SPL_CUDA(cudaMemcpyAsync(h_image, c->host_img_scratch.p, nv * sizeof(float),
+                             cudaMemcpyDeviceToHost, c->stream));
+    SPL_CUDA(cudaStreamSynchronize(c->stream));
+    return SPL_OK;
+}
+
+extern "C" int spl_render_batch(spl_ctx *c, const spl_camera *cams, int32_t n_views,
+                                float *const *d_images, void *stream) {
+    if (!c || !cams || !d_images || n_views < 0) return SPL_EINVAL;
+    for (int v = 0; v < n_views; ++v)
+        if (!camera_ok(&cams[v]) || !d_images[v]) return SPL_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    for (int v = 0; v < n_views; ++v) SPL_TRY(render_frame(c, cams[v], d_images[v], s));
+    return SPL_OK;
+}
+
+extern "C" int spl_get_records(spl_ctx *c, int64_t n, double *xs, double *ys, float *r, float *e,
+                               int32_t *cls) {
+    if (!c || n < 0 || n > c->n) return SPL_EINVAL;
+    if (n == 0) return SPL_OK;
+    if ((size_t)n > c->rec0.cap || (size_t)n > c->rec1.cap) return SPL_ESTATE;
+    DeviceGuard g(c->device);
+    float4 *h0 = new (std::nothrow) float4[n];
+    float4 *h1 = new (std::nothrow) float4[n];
+    if (!h0 || !h1) {
+        delete[] h0;
+        delete[] h1;
+        return SPL_ENOMEM;
+    }
+    int rc = cuda_status(cudaStreamSynchronize(c->stream));
+    if (rc == SPL_OK) rc = cuda_status(cudaMemcpy(h0, c->rec0.p, n * sizeof(float4), cudaMemcpyDeviceToHost));
+    if (rc == SPL_OK) rc = cuda_status(cudaMemcpy(h1, c->rec1.p, n * sizeof(float4), cudaMemcpyDeviceToHost));
+    if (rc == SPL_OK) {
+        const double rs2 = (double)(float)(c->par.r_sml * c->par.r_sml);
+        const double rm2 = (double)(float)(c->par.r_small * c->par.r_small);
+        const double rl2 = (double)(float)(c->par.r_large * c->par.r_large);
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t bits;
+            std::memcpy(&bits, &h0[i].x, 4);
+            const int xi = (int)(int16_t)(bits & 0xFFFFu), yi = ((int32_t)bits) >> 16;
+            const float r2 = h1[i].x;
+            if (xs) xs[i] = r2 < 0 ? 0.0 : (double)xi + (double)h0[i].y;
+            if (ys) ys[i] = r2 < 0 ? 0.0 : (double)yi + (double)h0[i].z;
+            if (r) r[i] = r2 < 0 ? 0.f : std::sqrt(r2);
+            if (e) {
+                e[3 * i] = h1[i].y;
+                e[3 * i + 1] = h1[i].z;
+                e[3 * i + 2] = h1[i].w;
+            }
+            if (cls)
+                cls[i] = r2 < 0 ? CLS_INACTIVE
+                                : (r2 <= rs2 ? CLS_POINT
+                                             : (r2 <= rm2 ? CLS_SMALL : (r2 <= rl2 ? CLS_MEDIUM : CLS_LARGE)));
+        }
+    }
+    delete[] h0;
+    delete[] h1;
+    return rc;
+}
+
+extern "C" int spl_count_work(spl_ctx *c, int64_t out[4]) {
+    if (!c || !out) return SPL_EINVAL;
+    if (!c->have_particles || !c->have_cam || c->npal < 1) return SPL_ESTATE;
+    DeviceGuard g(c->device);
+    const FrameConst fc = make_frame(c, c->cam);
+    const size_t n = (size_t)c->n;
+    SPL_TRY(c->rec0.ensure(n ? n : 1));
+    SPL_TRY(c->rec1.ensure(n ? n : 1));
+    SPL_TRY(c->large_ids.ensure(n ? n : 1));
+    SPL_TRY(c->counts.ensure((size_t)NLIST * fc.ntiles));
+    DevBuf<unsigned long long> work;
+    SPL_TRY(work.ensure(4));
+    int rc = SPL_OK;
+    cudaStream_t s = c->stream;
+    if (rc == SPL_OK) rc = cuda_status(cudaMemsetAsync(work.p, 0, 4 * sizeof(unsigned long long), s));
+    if (rc == SPL_OK) rc = cuda_status(cudaMemsetAsync(c->counts.p, 0, sizeof(int) * NLIST * fc.ntiles, s));
+    if (rc == SPL_OK) rc = cuda_status(cudaMemsetAsync(c->dstats.p, 0, offsetof(DevStats, err), s));
+    if (rc == SPL_OK) {
+        RasterArgs ra{};
+        ra.n = c->n;
+        ra.x = c->x.p; ra.y = c->y.p; ra.z = c->z.p;
+        ra.h = c->h.p; ra.I = c->I.p; ra.s = c->s.p;
+        ra.pal = c->pal.p;
+        ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
+        ra.counts = c->counts.p;
+        ra.large_ids = c->large_ids.p;
+        ra.st = c->dstats.p;
+        launch_raster(fc, ra, c->attr_type == SPL_ATTR_F16, c->sms, s);
+        launch_count_work(fc, c->rec0.p, c->rec1.p, c->n, work.p, c->sms, s);
+        unsigned long long h[4] = {0, 0, 0, 0};
+        rc = cuda_status(cudaGetLastError());
+        if (rc == SPL_OK) rc = cuda_status(cudaMemcpyAsync(h, work.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        if (rc == SPL_OK) rc = cuda_status(cudaStreamSynchronize(s));
+        for (int k = 0; k < 4; ++k) out[k] = (int64_t)h[k];
+    }
+    work.release();
+    return rc;
+}

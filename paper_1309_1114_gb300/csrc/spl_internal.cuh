@@ -1,0 +1,103 @@
+// spl_internal.cuh -- shared declarations of the GB300 Splotch renderer.
+//
+// Data layout in HBM (one frame):
+//   particles   SoA: x, y, z (FP32) and h, I, s (FP32 or binary16), owned by the
+//               context, read once per frame by the rasteriser.
+//   records     two float4 arrays indexed by particle id (32 B per particle):
+//                 rec0 = { packed (xi, yi) as two int16, xf, yf, kq }
+//                 rec1 = { r^2 (negative when inactive), e_R, e_G, e_B }
+//               where x_s = xi + xf with xf in [0, 1) (the integer part keeps
+//               the sub-pixel position exact to ~1e-7 px in FP32) and
+//               kq = log2(e) / sigma_s^2, so exp(-d^2/sigma^2) = 2^(-kq d^2).
+//   counts      int32 [NLIST][n_tiles]: entries per (list, tile), then an
+//               exclusive scan into offsets [NLIST * n_tiles + 1].
+//   entries     uint32 particle ids, grouped by list, then by tile.
+//   image       caller-owned H x W x 3 FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace spl {
+
+// Lists a particle can be binned into (Sec. 4 classes by screen radius).
+enum : int { L_POINT = 0, L_SMALL = 1, L_MEDIUM = 2, L_LARGE = 3, NLIST = 4 };
+enum : int { CLS_INACTIVE = -2, CLS_POINT = 0, CLS_SMALL = 1, CLS_MEDIUM = 2, CLS_LARGE = 3 };
+
+// Device-side error bits (reported as SPL_EDEVICE).
+enum : unsigned { ERR_LIST_OVERFLOW = 1u, ERR_INDEX = 2u };
+
+constexpr int kMaxPalette = 1024;
+constexpr int kTileThreads = 256;        // 8 warps per tile CTA
+
+// Per-frame constants (camera in double-float: hi + lo pairs of FP32).
+struct FrameConst {
+    float Rhi[9], Rlo[9];      // rows right, up', fwd
+    float Ehi[3], Elo[3];      // R * eye
+    float fhi, flo;            // focal length
+    float half_w, half_h;
+    float z_near;
+    float sig_fac;             // sigma_per_h / s_box
+    float chi;
+    float r_sml2, r_small2, r_large2;   // squared class radii
+    float s_min, s_inv;        // colour-scalar normalisation
+    float brightness;
+    int npal;
+    int width, height;
+    int tile, ntx, nty, ntiles;
+};
+
+// Device status block (one per context).
+// Everything before `err` is cleared at the start of every frame; `err`
+// accumulates until the host reads and clears it.
+struct DevStats {
+    unsigned long long n_active, n_point, n_small, n_medium, n_large;
+    unsigned int n_large_ids;  // large particles appended this frame
+    int totals[NLIST];         // entries per list (written by the scan)
+    unsigned int err;          // ERR_* bits
+};
+
+struct RasterArgs {
+    int64_t n;
+    const float *x, *y, *z;
+    const void *h, *I, *s;
+    const float *pal;          // npal * 3
+    float4 *rec0, *rec1;
+    int *counts;               // [NLIST][ntiles]
+    unsigned *large_ids;       // capacity n
+    DevStats *st;
+};
+
+struct BinArgs {
+    int64_t n;
+    const float4 *rec0, *rec1;
+    const unsigned *large_ids;
+    int *cursor;               // [NLIST][ntiles], starts as the offsets
+    int *counts;
+    unsigned *entries;
+    int64_t entries_cap;
+    DevStats *st;
+};
+
+struct TileArgs {
+    const float4 *rec0, *rec1;
+    const int *offsets;        // [NLIST * ntiles + 1]
+    const unsigned *entries;
+    float *image;
+    DevStats *st;
+};
+
+// Launchers (stream-ordered, no synchronisation).
+void launch_raster(const FrameConst &fc, const RasterArgs &a, bool f16, int sms, cudaStream_t s);
+void launch_count_large(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s);
+void launch_scan(const FrameConst &fc, int *counts, int *offsets, int *cursor, DevStats *st,
+                 cudaStream_t s);
+void launch_scatter(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s);
+void launch_tile_pass(const FrameConst &fc, const TileArgs &a, cudaStream_t s);
+void launch_large_pass(const FrameConst &fc, const TileArgs &a, cudaStream_t s);
+void launch_epilogue_ea(float *image, int64_t nvals, int sms, cudaStream_t s);
+void launch_count_work(const FrameConst &fc, const float4 *rec0, const float4 *rec1, int64_t n,
+                       unsigned long long *work, int sms, cudaStream_t s);
+
+}  // namespace spl

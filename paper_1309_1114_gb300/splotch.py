@@ -1,0 +1,259 @@
+"""ctypes binding of ``include/splotch.h`` (argument marshalling only).
+
+Every function of the C ABI is exposed under its own name (``spl_create``,
+``spl_render`` ...); ``Renderer`` is a small convenience wrapper that takes
+torch tensors and numpy arrays.  All computation happens in the CUDA library
+``lib/libsplotch.so``; if it is missing or cannot be loaded, importing the
+library raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libsplotch.so")
+
+SPL_OK, SPL_EINVAL, SPL_ENOMEM, SPL_ECUDA, SPL_ESTATE, SPL_EDEVICE = range(6)
+SPL_MEM_HOST, SPL_MEM_DEVICE = 0, 1
+SPL_ATTR_F32, SPL_ATTR_F16 = 0, 1
+SPL_MODE_ADDITIVE, SPL_MODE_EA = 0, 1
+SPL_SCHED_NONE, SPL_SCHED_COUNT, SPL_SCHED_MLP = 0, 1, 2
+
+
+class spl_particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("h", C.c_void_p), ("I", C.c_void_p), ("s", C.c_void_p),
+                ("attr_type", C.c_int32), ("mem_space", C.c_int32)]
+
+
+class spl_camera(C.Structure):
+    _fields_ = [("eye", C.c_double * 3), ("target", C.c_double * 3), ("up", C.c_double * 3),
+                ("fov_y_deg", C.c_double), ("width", C.c_int32), ("height", C.c_int32),
+                ("z_near", C.c_double)]
+
+
+class spl_params(C.Structure):
+    _fields_ = [("chi", C.c_double), ("sigma_per_h", C.c_double), ("s_box", C.c_double),
+                ("r_sml", C.c_double), ("brightness", C.c_double), ("tile_px", C.c_int32),
+                ("r_small", C.c_double), ("r_large", C.c_double), ("mode", C.c_int32),
+                ("sched", C.c_int32)]
+
+
+class spl_stats(C.Structure):
+    _fields_ = [("n_particles", C.c_int64), ("n_active", C.c_int64), ("n_point", C.c_int64),
+                ("n_small", C.c_int64), ("n_medium", C.c_int64), ("n_large", C.c_int64),
+                ("n_entries", C.c_int64 * 4), ("n_tiles", C.c_int32), ("tile_px", C.c_int32),
+                ("ms_raster", C.c_float), ("ms_bin", C.c_float), ("ms_tile", C.c_float),
+                ("ms_large", C.c_float), ("ms_epilogue", C.c_float), ("ms_total", C.c_float),
+                ("timed_frames", C.c_int64), ("sum_ms", C.c_double * 6), ("launches", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["n_entries"] = list(self.n_entries)
+        d["sum_ms"] = list(self.sum_ms)
+        return d
+
+
+_P = C.c_void_p
+_SIGS = {
+    "spl_create": [C.POINTER(C.c_void_p), C.c_int, _P],
+    "spl_destroy": [_P],
+    "spl_load_particles": [_P, C.POINTER(spl_particles)],
+    "spl_set_camera": [_P, C.POINTER(spl_camera)],
+    "spl_set_colormap": [_P, _P, C.c_int32, C.c_float, C.c_float],
+    "spl_default_params": [C.POINTER(spl_params)],
+    "spl_set_params": [_P, C.POINTER(spl_params)],
+    "spl_get_params": [_P, C.POINTER(spl_params)],
+    "spl_render": [_P, _P, _P],
+    "spl_render_host": [_P, _P],
+    "spl_render_batch": [_P, C.POINTER(spl_camera), C.c_int32, C.POINTER(C.c_void_p), _P],
+    "spl_get_stats": [_P, C.POINTER(spl_stats)],
+    "spl_set_timing": [_P, C.c_int32],
+    "spl_get_records": [_P, C.c_int64, _P, _P, _P, _P, _P],
+    "spl_count_work": [_P, C.POINTER(C.c_int64)],
+    "spl_error_string": [C.c_int],
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsplotch.so (raises OSError when it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = C.CDLL(path)
+        for name, args in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = C.c_char_p if name == "spl_error_string" else C.c_int
+        _lib = lib
+    return _lib
+
+
+class SplotchError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = load_library().spl_error_string(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+def check(code: int, where: str) -> None:
+    if code != SPL_OK:
+        raise SplotchError(code, where)
+
+
+def _exported(name):
+    def call(*args):
+        return getattr(load_library(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+for _name in _SIGS:
+    globals()[_name] = _exported(_name)
+
+
+# ---------------------------------------------------------------- helpers
+def make_camera(cam: dict) -> spl_camera:
+    c = spl_camera()
+    c.eye[:] = [float(v) for v in cam["eye"]]
+    c.target[:] = [float(v) for v in cam["target"]]
+    c.up[:] = [float(v) for v in cam["up"]]
+    c.fov_y_deg = float(cam["fov_y_deg"])
+    c.width = int(cam["width"])
+    c.height = int(cam["height"])
+    c.z_near = float(cam.get("z_near", 1e-3))
+    return c
+
+
+def default_params(**over) -> spl_params:
+    q = spl_params()
+    check(load_library().spl_default_params(C.byref(q)), "spl_default_params")
+    for k, v in over.items():
+        if not hasattr(q, k):
+            raise KeyError(k)
+        setattr(q, k, v)
+    return q
+
+
+def _ptr(t):
+    """Address of a torch tensor or a numpy array."""
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+class Renderer:
+    """One library context on one device and stream.
+
+    ``load`` takes a dict of six arrays (x, y, z, h, I, s); numpy arrays are
+    copied from host memory, CUDA tensors from device memory.  ``render``
+    writes into a caller-owned CUDA float32 tensor of shape (H, W, 3).
+    """
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        lib = load_library()
+        h = C.c_void_p()
+        check(lib.spl_create(C.byref(h), int(device), stream), "spl_create")
+        self._h = h
+        self.device = device
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().spl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def load(self, parts: dict, fp16: dict | None = None):
+        """Load particles; fp16 (optional) holds h, I, s as binary16 arrays."""
+        src = dict(parts)
+        attr = SPL_ATTR_F32
+        if fp16 is not None:
+            src.update(fp16)
+            attr = SPL_ATTR_F16
+        arrs = [src[k] for k in ("x", "y", "z", "h", "I", "s")]
+        on_dev = [hasattr(a, "is_cuda") and a.is_cuda for a in arrs]
+        if any(on_dev) and not all(on_dev):
+            raise ValueError("particle arrays must all be on the host or all on the device")
+        n = int(arrs[0].shape[0])
+        if not any(on_dev):
+            arrs = [np.ascontiguousarray(a) for a in arrs]
+            for a, want in zip(arrs, [np.float32] * 3 + [np.float16 if attr else np.float32] * 3):
+                if a.dtype != want or a.shape != (n,):
+                    raise ValueError("particle arrays: wrong dtype or shape")
+        p = spl_particles(n, *[_ptr(a) for a in arrs], attr,
+                          SPL_MEM_DEVICE if any(on_dev) else SPL_MEM_HOST)
+        check(load_library().spl_load_particles(self._h, C.byref(p)), "spl_load_particles")
+
+    def set_camera(self, cam: dict):
+        c = make_camera(cam)
+        check(load_library().spl_set_camera(self._h, C.byref(c)), "spl_set_camera")
+        self.cam = dict(cam)
+
+    def set_colormap(self, pal, s_min: float = 0.0, s_max: float = 1.0):
+        pal = np.ascontiguousarray(pal, dtype=np.float32).reshape(-1, 3)
+        check(load_library().spl_set_colormap(self._h, pal.ctypes.data, pal.shape[0],
+                                              float(s_min), float(s_max)), "spl_set_colormap")
+
+    def set_params(self, **kw):
+        q = default_params(**kw)
+        check(load_library().spl_set_params(self._h, C.byref(q)), "spl_set_params")
+
+    def set_timing(self, on: bool = True):
+        check(load_library().spl_set_timing(self._h, int(bool(on))), "spl_set_timing")
+
+    def render(self, image, stream: int | None = None):
+        check(load_library().spl_render(self._h, image.data_ptr(), stream), "spl_render")
+        return image
+
+    def render_host(self, out: np.ndarray | None = None) -> np.ndarray:
+        shape = (self.cam["height"], self.cam["width"], 3)
+        if out is None:
+            out = np.empty(shape, dtype=np.float32)
+        if out.shape != shape or out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise ValueError("render_host: out must be a contiguous float32 (H, W, 3) array")
+        check(load_library().spl_render_host(self._h, out.ctypes.data), "spl_render_host")
+        return out
+
+    def render_batch(self, cams: list, images: list, stream: int | None = None):
+        arr = (spl_camera * len(cams))(*[make_camera(c) for c in cams])
+        ptrs = (C.c_void_p * len(images))(*[im.data_ptr() for im in images])
+        check(load_library().spl_render_batch(self._h, arr, len(cams), ptrs, stream),
+              "spl_render_batch")
+        return images
+
+    def stats(self) -> dict:
+        s = spl_stats()
+        check(load_library().spl_get_stats(self._h, C.byref(s)), "spl_get_stats")
+        return s.as_dict()
+
+    def count_work(self) -> list:
+        out = (C.c_int64 * 4)()
+        check(load_library().spl_count_work(self._h, out), "spl_count_work")
+        return list(out)
+
+    def records(self, n: int) -> dict:
+        xs = np.zeros(n)
+        ys = np.zeros(n)
+        r = np.zeros(n, np.float32)
+        e = np.zeros((n, 3), np.float32)
+        cls = np.zeros(n, np.int32)
+        check(load_library().spl_get_records(self._h, n, xs.ctypes.data, ys.ctypes.data,
+                                             r.ctypes.data, e.ctypes.data, cls.ctypes.data),
+              "spl_get_records")
+        return {"xs": xs, "ys": ys, "r": r, "e": e, "cls": cls}
