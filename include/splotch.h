@@ -103,7 +103,7 @@ typedef struct {
     double s_box;              /* S_box of Eq. 7 (default 1) */
     double r_sml;              /* point rule for r <= r_sml (default 0.5) */
     double brightness;         /* emission scale (default 1) */
-    int32_t tile_px;           /* tile side t_x = t_y of Eq. 8: 16 or 32 (default 32) */
+    int32_t tile_px;           /* tile side t_x = t_y of Eq. 8: 16, 32 or 64 (default 32) */
     double r_small;            /* r_sml < r <= r_small: one thread per particle (default 4) */
     double r_large;            /* r > r_large: large pass (default 64) */
     int32_t mode;              /* SPL_MODE_ADDITIVE or SPL_MODE_EA */

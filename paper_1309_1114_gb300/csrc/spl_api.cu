@@ -72,6 +72,8 @@ struct spl_ctx {
     DevBuf<float4> rec0, rec1;
     DevBuf<int> counts, offsets, cursor;
     DevBuf<unsigned> large_ids, entries;
+    DevBuf<int> item_counts, item_offsets;
+    DevBuf<WorkItem> items;
     DevBuf<DevStats> dstats;
     DevBuf<float> host_img_scratch;
     DevStats *hstats = nullptr;   // pinned
@@ -131,7 +133,7 @@ static bool params_ok(const spl_params *q) {
     return q && std::isfinite(q->chi) && q->chi > 0 && std::isfinite(q->sigma_per_h) &&
            q->sigma_per_h > 0 && std::isfinite(q->s_box) && q->s_box > 0 &&
            std::isfinite(q->r_sml) && q->r_sml >= 0 && std::isfinite(q->brightness) &&
-           (q->tile_px == 16 || q->tile_px == 32) && std::isfinite(q->r_small) &&
+           (q->tile_px == 16 || q->tile_px == 32 || q->tile_px == 64) && std::isfinite(q->r_small) &&
            q->r_small >= q->r_sml && std::isfinite(q->r_large) && q->r_large >= q->r_small &&
            (q->mode == SPL_MODE_ADDITIVE || q->mode == SPL_MODE_EA) && q->sched >= 0 &&
            q->sched <= SPL_SCHED_MLP;
@@ -195,6 +197,7 @@ extern "C" int spl_destroy(spl_ctx *c) {
     c->rec0.release(); c->rec1.release();
     c->counts.release(); c->offsets.release(); c->cursor.release();
     c->large_ids.release(); c->entries.release(); c->dstats.release();
+    c->item_counts.release(); c->item_offsets.release(); c->items.release();
     c->host_img_scratch.release();
     if (c->hstats) cudaFreeHost(c->hstats);
     for (auto &set : c->ev)
@@ -389,6 +392,8 @@ static int render_frame(spl_ctx *c, const spl_camera &cam, float *d_image, cudaS
     SPL_TRY(c->counts.ensure((size_t)NLIST * fc.ntiles));
     SPL_TRY(c->offsets.ensure((size_t)NLIST * fc.ntiles + 1));
     SPL_TRY(c->cursor.ensure((size_t)NLIST * fc.ntiles));
+    SPL_TRY(c->item_counts.ensure((size_t)2 * fc.ntiles));
+    SPL_TRY(c->item_offsets.ensure((size_t)2 * fc.ntiles + 1));
     SPL_TRY(c->entries.ensure(16));
     SPL_CUDA(cudaGetLastError());
 
@@ -414,7 +419,11 @@ static int render_frame(spl_ctx *c, const spl_camera &cam, float *d_image, cudaS
     ba.cursor = c->cursor.p;
     ba.st = c->dstats.p;
     launch_count_large(fc, ba, c->sms, s);
-    launch_scan(fc, c->counts.p, c->offsets.p, c->cursor.p, c->dstats.p, s);
+    launch_scan(NLIST * fc.ntiles, c->counts.p, c->offsets.p, c->cursor.p, NLIST,
+                c->dstats.p->totals, s);
+    launch_item_counts(fc, c->offsets.p, c->item_counts.p, s);
+    launch_scan(2 * fc.ntiles, c->item_counts.p, c->item_offsets.p, nullptr, 2,
+                c->dstats.p->item_totals, s);
     SPL_CUDA(cudaGetLastError());
     SPL_CUDA(cudaMemcpyAsync(c->hstats, c->dstats.p, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
     SPL_CUDA(cudaStreamSynchronize(s));
@@ -427,28 +436,34 @@ static int render_frame(spl_ctx *c, const spl_camera &cam, float *d_image, cudaS
     int64_t total = 0;
     for (int k = 0; k < NLIST; ++k) total += c->hstats->totals[k];
     if (total > (int64_t)0x7FFFFFFF) return SPL_ENOMEM;   // list positions are int32
+    const int n_tile_items = c->hstats->item_totals[0];
+    const int n_large_items = c->hstats->item_totals[1];
     SPL_TRY(c->entries.ensure((size_t)(total ? total : 1)));
+    SPL_TRY(c->items.ensure((size_t)(n_tile_items + n_large_items + 1)));
+    SPL_CUDA(cudaMemsetAsync(d_image, 0, sizeof(float) * 3 * (size_t)cam.width * cam.height, s));
     ba.entries = c->entries.p;
     ba.entries_cap = (int64_t)c->entries.cap;
     launch_scatter(fc, ba, c->sms, s);
+    launch_fill_items(fc, c->offsets.p, c->item_offsets.p, c->items.p, s);
     record_event(c, 2, s);
     TileArgs ta{};
     ta.rec0 = c->rec0.p; ta.rec1 = c->rec1.p;
     ta.offsets = c->offsets.p;
     ta.entries = c->entries.p;
+    ta.items = c->items.p;
     ta.image = d_image;
     ta.st = c->dstats.p;
-    launch_tile_pass(fc, ta, s);
+    launch_tile_pass(fc, ta, n_tile_items, c->sms, s);
     record_event(c, 3, s);
-    if (c->hstats->totals[L_LARGE] > 0) launch_large_pass(fc, ta, s);
+    launch_large_pass(fc, ta, n_tile_items, n_large_items, c->sms, s);
     record_event(c, 4, s);
     if (c->par.mode == SPL_MODE_EA)
         launch_epilogue_ea(d_image, (int64_t)3 * cam.width * cam.height, c->sms, s);
     record_event(c, 5, s);
     SPL_CUDA(cudaGetLastError());
 
-    int launches = 2 + (c->n > 0 ? 4 : 0);
-    if (c->hstats->totals[L_LARGE] > 0) launches += 1;
+    int launches = 4 + (c->n > 0 ? 4 : 0) + (n_tile_items > 0 ? 1 : 0);
+    if (n_large_items > 0) launches += 1;
     if (c->par.mode == SPL_MODE_EA) launches += 1;
     if (c->timing) {
         c->ev_pending[c->ev_set] = true;

@@ -54,9 +54,22 @@ struct FrameConst {
 struct DevStats {
     unsigned long long n_active, n_point, n_small, n_medium, n_large;
     unsigned int n_large_ids;  // large particles appended this frame
-    int totals[NLIST];         // entries per list (written by the scan)
+    int totals[NLIST];         // entries per list (written by the first scan)
+    int item_totals[2];        // work items of the tile pass and of the large pass
+    int item_counter[2];       // dynamic work-item counters of the two passes
     unsigned int err;          // ERR_* bits
 };
+
+// A work item of the persistent tile / large passes: a tile and a range of
+// one of its lists, or (list == -1) every list of a tile light enough to be
+// done by one CTA, which then stores its pixels instead of adding them.
+struct WorkItem {
+    int tile, list, start, end;
+};
+
+// Largest list segment one work item takes (per list), so that a crowded
+// tile (a halo core holding 1e5-1e6 particles) is spread over many CTAs.
+constexpr int kSegPoint = 8192, kSegSmall = 2048, kSegMedium = 1024, kSegLarge = 512;
 
 struct RasterArgs {
     int64_t n;
@@ -84,6 +97,7 @@ struct TileArgs {
     const float4 *rec0, *rec1;
     const int *offsets;        // [NLIST * ntiles + 1]
     const unsigned *entries;
+    const WorkItem *items;
     float *image;
     DevStats *st;
 };
@@ -91,11 +105,18 @@ struct TileArgs {
 // Launchers (stream-ordered, no synchronisation).
 void launch_raster(const FrameConst &fc, const RasterArgs &a, bool f16, int sms, cudaStream_t s);
 void launch_count_large(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s);
-void launch_scan(const FrameConst &fc, int *counts, int *offsets, int *cursor, DevStats *st,
+// Exclusive scan of in[0..m) into out[0..m] (out[m] = total); cursor (may be
+// null) receives a copy of out[0..m); seg_totals[k] = total of the k-th of
+// nseg equal segments.
+void launch_scan(int m, const int *in, int *out, int *cursor, int nseg, int *seg_totals,
                  cudaStream_t s);
+void launch_item_counts(const FrameConst &fc, const int *offsets, int *item_counts, cudaStream_t s);
+void launch_fill_items(const FrameConst &fc, const int *offsets, const int *item_offsets,
+                       WorkItem *items, cudaStream_t s);
 void launch_scatter(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s);
-void launch_tile_pass(const FrameConst &fc, const TileArgs &a, cudaStream_t s);
-void launch_large_pass(const FrameConst &fc, const TileArgs &a, cudaStream_t s);
+void launch_tile_pass(const FrameConst &fc, const TileArgs &a, int n_items, int sms, cudaStream_t s);
+void launch_large_pass(const FrameConst &fc, const TileArgs &a, int item0, int n_items, int sms,
+                       cudaStream_t s);
 void launch_epilogue_ea(float *image, int64_t nvals, int sms, cudaStream_t s);
 void launch_count_work(const FrameConst &fc, const float4 *rec0, const float4 *rec1, int64_t n,
                        unsigned long long *work, int sms, cudaStream_t s);

@@ -126,47 +126,118 @@ __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spa
     return record_class(fc, r1.x);
 }
 
-// Count the tile-list entries of one rasterised particle (points, small and
-// medium; large particles are counted by count_large_kernel).
-__device__ __forceinline__ void count_entries(const FrameConst &fc, int cls, float4 r0, float4 r1,
-                                              int *counts) {
+// Tile footprint of one rasterised particle for the point / small / medium
+// lists: a box of tiles [tx0, tx0 + bw) x [ty0, ty0 + nbox / bw) (nbox = 0:
+// no entry).  Large particles are handled by large_tiles_kernel.
+struct TileFoot { int list, tx0, ty0, bw, nbox; };
+
+__device__ __forceinline__ TileFoot tile_footprint(const FrameConst &fc, int cls, float4 r0, float4 r1) {
+    TileFoot f{-1, 0, 0, 1, 0};
     if (cls == CLS_POINT) {
         const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
-        if (xi >= 0 && yi >= 0 && xi < fc.width && yi < fc.height)
-            atomicAdd(&counts[L_POINT * fc.ntiles + (yi / fc.tile) * fc.ntx + xi / fc.tile], 1);
-        return;
+        if (xi >= 0 && yi >= 0 && xi < fc.width && yi < fc.height) {
+            f.list = L_POINT; f.tx0 = xi / fc.tile; f.ty0 = yi / fc.tile; f.nbox = 1;
+        }
+        return f;
     }
-    if (cls != CLS_SMALL && cls != CLS_MEDIUM) return;
+    if (cls != CLS_SMALL && cls != CLS_MEDIUM) return f;
     PixBox b;
-    if (!splat_box(fc, r0, r1.x, b)) return;
-    const int list = cls == CLS_SMALL ? L_SMALL : L_MEDIUM;
-    for (int ty = b.j0 / fc.tile; ty <= b.j1 / fc.tile; ++ty)
-        for (int tx = b.i0 / fc.tile; tx <= b.i1 / fc.tile; ++tx)
-            if (disc_meets_tile(fc, r0, r1.x, tx, ty))
-                atomicAdd(&counts[list * fc.ntiles + ty * fc.ntx + tx], 1);
+    if (!splat_box(fc, r0, r1.x, b)) return f;
+    f.list = cls == CLS_SMALL ? L_SMALL : L_MEDIUM;
+    f.tx0 = b.i0 / fc.tile;
+    f.ty0 = b.j0 / fc.tile;
+    f.bw = b.i1 / fc.tile - f.tx0 + 1;
+    f.nbox = f.bw * (b.j1 / fc.tile - f.ty0 + 1);
+    return f;
+}
+
+// Slot (list * ntiles + tile) of the k-th tile of a footprint, or -1 when
+// k is past the box or the disc misses that tile.
+__device__ __forceinline__ int foot_slot(const FrameConst &fc, const TileFoot &f, int k, float4 r0,
+                                         float4 r1) {
+    if (k >= f.nbox) return -1;
+    const int tx = f.tx0 + k % f.bw, ty = f.ty0 + k / f.bw;
+    if (f.list != L_POINT && !disc_meets_tile(fc, r0, r1.x, tx, ty)) return -1;
+    return f.list * fc.ntiles + ty * fc.ntx + tx;
+}
+
+// ---------------------------------------------------------------------------
+// Per-CTA aggregation of list slots.  A clustered particle set puts 1e5-1e6
+// entries into single tiles; one global atomic per entry then serialises in
+// L2.  Each CTA takes a contiguous chunk of particles, combines the entries
+// of a warp that share a slot (match), and accumulates the rest in a small
+// shared-memory hash table (open addressing, key = list * ntiles + tile), so
+// that a hot slot receives one global atomic per CTA.  A key that finds no
+// free place within kProbe probes falls back to global atomics; the table is
+// never emptied while a CTA runs, so that choice is the same for every
+// occurrence of the key within the CTA.
+// ---------------------------------------------------------------------------
+constexpr int kHash = 4096;          // slots (power of two)
+constexpr int kProbe = 32;
+constexpr int kChunk = 4096;         // particles per CTA in the binning kernels
+
+__device__ __forceinline__ int hash_slot(const int *keys, int key, bool insert) {
+    unsigned h = ((unsigned)key * 2654435761u) >> 20;
+    for (int probe = 0; probe < kProbe; ++probe) {
+        const int slot = (int)((h + (unsigned)probe) & (kHash - 1));
+        const int k = *(volatile const int *)&keys[slot];
+        if (k == key) return slot;
+        if (k == -1) {
+            if (!insert) return -1;
+            const int old = atomicCAS((int *)&keys[slot], -1, key);
+            if (old == -1 || old == key) return slot;
+        }
+    }
+    return -1;
+}
+
+// Count the slots of one round (k-th tile of every lane's footprint).
+__device__ __forceinline__ void count_round(int key, int *keys, int *vals, int *gcounts, int lane) {
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(m) - 1) {
+        const int slot = hash_slot(keys, key, true);
+        if (slot >= 0)
+            atomicAdd(&vals[slot], __popc(m));
+        else
+            atomicAdd(&gcounts[key], __popc(m));
+    }
+}
+
+__device__ __forceinline__ void hash_clear(int *keys, int *vals) {
+    for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
+        keys[k] = -1;
+        vals[k] = 0;
+    }
 }
 
 template <bool F16>
 __global__ void __launch_bounds__(256) raster_kernel(FrameConst fc, RasterArgs a) {
     __shared__ float spal[3 * kMaxPalette];
+    __shared__ int keys[kHash], vals[kHash];
+    __shared__ unsigned long long bstat[5];
     for (int k = threadIdx.x; k < 3 * fc.npal; k += blockDim.x) spal[k] = a.pal[k];
+    hash_clear(keys, vals);
+    if (threadIdx.x < 5) bstat[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     unsigned n_act = 0, n_pt = 0, n_sm = 0, n_md = 0, n_lg = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * kChunk;
+    const int64_t c1 = c0 + kChunk < a.n ? c0 + kChunk : a.n;
     // all lanes of a warp run the same number of iterations (warp collectives)
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+    for (int64_t base = c0; base < c1; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
-        const bool valid = i < a.n;
+        const bool valid = i < c1;
         int cls = CLS_INACTIVE;
-        float4 r0, r1;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
         if (valid) {
             cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_attr<F16>(a.h, i),
                              load_attr<F16>(a.I, i), load_attr<F16>(a.s, i), r0, r1);
             a.rec0[i] = r0;
             a.rec1[i] = r1;
-            count_entries(fc, cls, r0, r1, a.counts);
         }
+        const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0};
+        const int maxk = __reduce_max_sync(0xffffffffu, foot.nbox);
+        for (int k = 0; k < maxk; ++k) count_round(foot_slot(fc, foot, k, r0, r1), keys, vals, a.counts, lane);
         n_act += cls != CLS_INACTIVE;
         n_pt += cls == CLS_POINT;
         n_sm += cls == CLS_SMALL;
@@ -189,18 +260,26 @@ __global__ void __launch_bounds__(256) raster_kernel(FrameConst fc, RasterArgs a
     n_md = __reduce_add_sync(0xffffffffu, n_md);
     n_lg = __reduce_add_sync(0xffffffffu, n_lg);
     if (lane == 0) {
-        if (n_act) atomicAdd(&a.st->n_active, (unsigned long long)n_act);
-        if (n_pt) atomicAdd(&a.st->n_point, (unsigned long long)n_pt);
-        if (n_sm) atomicAdd(&a.st->n_small, (unsigned long long)n_sm);
-        if (n_md) atomicAdd(&a.st->n_medium, (unsigned long long)n_md);
-        if (n_lg) atomicAdd(&a.st->n_large, (unsigned long long)n_lg);
+        atomicAdd(&bstat[0], (unsigned long long)n_act);
+        atomicAdd(&bstat[1], (unsigned long long)n_pt);
+        atomicAdd(&bstat[2], (unsigned long long)n_sm);
+        atomicAdd(&bstat[3], (unsigned long long)n_md);
+        atomicAdd(&bstat[4], (unsigned long long)n_lg);
+    }
+    __syncthreads();
+    // flush: one global atomic per distinct slot of this CTA
+    for (int k = threadIdx.x; k < kHash; k += blockDim.x)
+        if (keys[k] >= 0) atomicAdd(&a.counts[keys[k]], vals[k]);
+    if (threadIdx.x < 5 && bstat[threadIdx.x]) {
+        // n_active .. n_large are consecutive fields of DevStats
+        atomicAdd(&a.st->n_active + threadIdx.x, bstat[threadIdx.x]);
     }
 }
 
 void launch_raster(const FrameConst &fc, const RasterArgs &a, bool f16, int sms, cudaStream_t s) {
+    (void)sms;
     if (a.n <= 0) return;
-    int64_t blocks = (a.n + 255) / 256;
-    blocks = blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8;
+    const int64_t blocks = (a.n + kChunk - 1) / kChunk;
     if (f16)
         raster_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
     else
@@ -248,17 +327,15 @@ void launch_count_large(const FrameConst &fc, const BinArgs &a, int sms, cudaStr
 }
 
 // ---------------------------------------------------------------------------
-// Exclusive scan of the (list, tile) counts: one CTA of 1024 threads, each
-// owning a contiguous run of slots.
+// Exclusive scan: one CTA of 1024 threads, each owning a contiguous run.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) scan_kernel(int m, int ntiles, const int *counts,
-                                                    int *offsets, int *cursor, DevStats *st) {
+__global__ void __launch_bounds__(1024) scan_kernel(int m, const int *in, int *out, int *cursor,
+                                                    int nseg, int *seg_totals) {
     __shared__ int wsum[32];
     const int t = threadIdx.x, per = (m + 1023) / 1024;
     const int lo = min(t * per, m), hi = min(lo + per, m);
     int sum = 0;
-    for (int k = lo; k < hi; ++k) sum += counts[k];
-    // block-wide exclusive scan of the per-thread sums
+    for (int k = lo; k < hi; ++k) sum += in[k];
     const int lane = t & 31, warp = t >> 5;
     int incl = sum;
 #pragma unroll
@@ -281,18 +358,77 @@ __global__ void __launch_bounds__(1024) scan_kernel(int m, int ntiles, const int
     __syncthreads();
     int run = wsum[warp] + incl - sum;
     for (int k = lo; k < hi; ++k) {
-        offsets[k] = run;
-        cursor[k] = run;
-        run += counts[k];
+        out[k] = run;
+        if (cursor) cursor[k] = run;
+        run += in[k];
     }
-    if (t == 1023) offsets[m] = run;
-    __syncthreads();   // makes every thread's offsets visible to the block
-    if (t < NLIST) st->totals[t] = offsets[(t + 1) * ntiles] - offsets[t * ntiles];
+    if (t == 1023) out[m] = run;
+    __syncthreads();   // makes every thread's results visible to the block
+    if (t < nseg) {
+        const int seg = m / nseg;
+        seg_totals[t] = out[(t + 1) * seg] - out[t * seg];
+    }
 }
 
-void launch_scan(const FrameConst &fc, int *counts, int *offsets, int *cursor, DevStats *st,
+void launch_scan(int m, const int *in, int *out, int *cursor, int nseg, int *seg_totals,
                  cudaStream_t s) {
-    scan_kernel<<<1, 1024, 0, s>>>(NLIST * fc.ntiles, fc.ntiles, counts, offsets, cursor, st);
+    scan_kernel<<<1, 1024, 0, s>>>(m, in, out, cursor, nseg, seg_totals);
+}
+
+// ---------------------------------------------------------------------------
+// Work items: a light tile is one item (all its lists, pixels stored); a
+// crowded tile is cut into segments of at most kSeg* entries per list, each
+// its own item (pixels added).  Large-list entries always form separate
+// items of the large pass.  item_counts = [tile-pass items | large items].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int div_up(int a, int b) { return (a + b - 1) / b; }
+
+__global__ void item_count_kernel(FrameConst fc, const int *off, int *item_counts) {
+    const int nt = fc.ntiles;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const int cp = off[L_POINT * nt + t + 1] - off[L_POINT * nt + t];
+        const int cs = off[L_SMALL * nt + t + 1] - off[L_SMALL * nt + t];
+        const int cm = off[L_MEDIUM * nt + t + 1] - off[L_MEDIUM * nt + t];
+        const int cl = off[L_LARGE * nt + t + 1] - off[L_LARGE * nt + t];
+        int n = 0;
+        if (cp + cs + cm > 0) {
+            if (cp <= kSegPoint && cs <= kSegSmall && cm <= kSegMedium)
+                n = 1;
+            else
+                n = div_up(cp, kSegPoint) + div_up(cs, kSegSmall) + div_up(cm, kSegMedium);
+        }
+        item_counts[t] = n;
+        item_counts[nt + t] = div_up(cl, kSegLarge);
+    }
+}
+
+void launch_item_counts(const FrameConst &fc, const int *offsets, int *item_counts, cudaStream_t s) {
+    item_count_kernel<<<(fc.ntiles + 255) / 256, 256, 0, s>>>(fc, offsets, item_counts);
+}
+
+__global__ void fill_items_kernel(FrameConst fc, const int *off, const int *ioff, WorkItem *items) {
+    const int nt = fc.ntiles;
+    const int seg[NLIST] = {kSegPoint, kSegSmall, kSegMedium, kSegLarge};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        int w = ioff[t];
+        const int nw = ioff[t + 1] - w;
+        if (nw == 1) {
+            items[w] = {t, -1, 0, 0};
+        } else if (nw > 1) {
+            for (int l = 0; l < L_LARGE; ++l) {
+                const int b = off[l * nt + t], e = off[l * nt + t + 1];
+                for (int k = b; k < e; k += seg[l]) items[w++] = {t, l, k, min(k + seg[l], e)};
+            }
+        }
+        int wl = ioff[nt + t];
+        const int b = off[L_LARGE * nt + t], e = off[L_LARGE * nt + t + 1];
+        for (int k = b; k < e; k += kSegLarge) items[wl++] = {t, L_LARGE, k, min(k + kSegLarge, e)};
+    }
+}
+
+void launch_fill_items(const FrameConst &fc, const int *offsets, const int *item_offsets,
+                       WorkItem *items, cudaStream_t s) {
+    fill_items_kernel<<<(fc.ntiles + 255) / 256, 256, 0, s>>>(fc, offsets, item_offsets, items);
 }
 
 // ---------------------------------------------------------------------------
@@ -300,39 +436,85 @@ void launch_scan(const FrameConst &fc, int *counts, int *offsets, int *cursor, D
 // tiles' lists (order inside a tile follows the atomics, which is harmless:
 // E_p = A_p makes the sum order-independent, Sec. 2).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ TileFoot load_foot(const FrameConst &fc, const BinArgs &a, int64_t i,
+                                              int64_t c1, float4 &r0, float4 &r1) {
+    r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
+    if (i >= c1) return TileFoot{-1, 0, 0, 1, 0};
+    r1 = a.rec1[i];
+    const int cls = record_class(fc, r1.x);
+    if (cls == CLS_INACTIVE || cls == CLS_LARGE) return TileFoot{-1, 0, 0, 1, 0};
+    r0 = a.rec0[i];
+    return tile_footprint(fc, cls, r0, r1);
+}
+
+// Scatter particle ids of points, small and medium particles into their
+// tiles' lists.  Per CTA: count its chunk's slots in the shared hash table,
+// reserve one contiguous range per slot with one global atomic, then place
+// every entry at range base + local rank.  Order inside a tile follows the
+// atomics, which is harmless: E_p = A_p makes the sum order-independent
+// (Sec. 2).
 __global__ void __launch_bounds__(256) scatter_kernel(FrameConst fc, BinArgs a) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        const float4 r1 = a.rec1[i];
-        const int cls = record_class(fc, r1.x);
-        if (cls == CLS_INACTIVE || cls == CLS_LARGE) continue;
-        const float4 r0 = a.rec0[i];
-        if (cls == CLS_POINT) {
-            const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
-            if (xi < 0 || yi < 0 || xi >= fc.width || yi >= fc.height) continue;
-            const int pos = atomicAdd(
-                &a.cursor[L_POINT * fc.ntiles + (yi / fc.tile) * fc.ntx + xi / fc.tile], 1);
-            if (pos < a.entries_cap) a.entries[pos] = (unsigned)i;
-            else atomicOr(&a.st->err, ERR_LIST_OVERFLOW);
-            continue;
-        }
-        PixBox b;
-        if (!splat_box(fc, r0, r1.x, b)) continue;
-        const int list = cls == CLS_SMALL ? L_SMALL : L_MEDIUM;
-        for (int ty = b.j0 / fc.tile; ty <= b.j1 / fc.tile; ++ty)
-            for (int tx = b.i0 / fc.tile; tx <= b.i1 / fc.tile; ++tx) {
-                if (!disc_meets_tile(fc, r0, r1.x, tx, ty)) continue;
-                const int pos = atomicAdd(&a.cursor[list * fc.ntiles + ty * fc.ntx + tx], 1);
-                if (pos < a.entries_cap) a.entries[pos] = (unsigned)i;
-                else atomicOr(&a.st->err, ERR_LIST_OVERFLOW);
+    __shared__ int keys[kHash], vals[kHash], bases[kHash];
+    hash_clear(keys, vals);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t c0 = (int64_t)blockIdx.x * kChunk;
+    const int64_t c1 = c0 + kChunk < a.n ? c0 + kChunk : a.n;
+    // pass 1: local counts
+    for (int64_t base = c0; base < c1; base += blockDim.x) {
+        float4 r0, r1;
+        const TileFoot f = load_foot(fc, a, base + threadIdx.x, c1, r0, r1);
+        const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
+        for (int k = 0; k < maxk; ++k) {
+            const int key = foot_slot(fc, f, k, r0, r1);
+            const unsigned m = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && lane == __ffs(m) - 1) {
+                const int slot = hash_slot(keys, key, true);
+                if (slot >= 0) atomicAdd(&vals[slot], __popc(m));
             }
+        }
+    }
+    __syncthreads();
+    // reserve one range per slot
+    for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
+        if (keys[k] >= 0) bases[k] = atomicAdd(&a.cursor[keys[k]], vals[k]);
+        vals[k] = 0;
+    }
+    __syncthreads();
+    // pass 2: place the entries
+    for (int64_t base = c0; base < c1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        float4 r0, r1;
+        const TileFoot f = load_foot(fc, a, i, c1, r0, r1);
+        const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
+        for (int k = 0; k < maxk; ++k) {
+            const int key = foot_slot(fc, f, k, r0, r1);
+            const unsigned m = __match_any_sync(0xffffffffu, key);
+            const int leader = __ffs(m) - 1;
+            int pos = 0;
+            if (key >= 0 && lane == leader) {
+                const int slot = hash_slot(keys, key, false);
+                if (slot >= 0)
+                    pos = bases[slot] + atomicAdd(&vals[slot], __popc(m));
+                else
+                    pos = atomicAdd(&a.cursor[key], __popc(m));
+            }
+            pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(m & lt);
+            if (key >= 0) {
+                if (pos < a.entries_cap)
+                    a.entries[pos] = (unsigned)i;
+                else
+                    atomicOr(&a.st->err, ERR_LIST_OVERFLOW);
+            }
+        }
     }
 }
 
 void launch_scatter(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s) {
     if (a.n <= 0) return;
-    int64_t blocks = (a.n + 255) / 256;
-    blocks = blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8;
+    const int64_t blocks = (a.n + kChunk - 1) / kChunk;
     scatter_kernel<<<(unsigned)blocks, 256, 0, s>>>(fc, a);
     large_tiles_kernel<1><<<sms * 2, 256, 0, s>>>(fc, a);
 }

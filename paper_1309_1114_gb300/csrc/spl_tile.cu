@@ -1,205 +1,371 @@
 // spl_tile.cu -- the rendering passes (Sec. 4.1-4.3 and Eq. 2).
 //
-// One CTA owns one T x T tile of the image (the tiling of Eq. 8) and is the
-// only writer of its pixels, so there are no races on the image and no global
-// atomics (the problem of Sec. 3.2.2 / Fig. 3).  Inside the CTA:
+// Work is cut into items: a T x T tile of the image (the tiling of Eq. 8)
+// together with its lists, or -- for a crowded tile, the load imbalance of
+// the Remarks of Sec. 4 -- a bounded segment of one of its lists.  Persistent
+// CTAs take items from a device counter.  A tile that is one item is written
+// by exactly one CTA with plain stores; the segments of a crowded tile add
+// their partial tiles into the (zeroed) image with one atomic add per pixel
+// and channel, instead of one per contribution (the write races of
+// Sec. 3.2.2 / Fig. 3).
+//
+// Inside an item every pixel of the tile has one owner thread: warp w owns a
+// band of T/8 rows, lane l owns the columns l (+32 for T = 64), and the
+// thread keeps its pixels' three channels in registers.  Then:
 //   - point particles (r <= r_sml, Sec. 4.1) add their emission to one pixel
-//     of a shared-memory copy of the tile (shared-memory atomics);
-//   - small particles (r_sml < r <= r_small): one thread per particle walks the
-//     particle's pixel box inside the tile, also into shared memory;
-//   - medium particles: one warp per particle; every warp keeps a private
-//     copy of the whole tile in registers (lane = column), so a particle costs
-//     one exp2 per lane for its column weight, one exp2 per row for the row
-//     weight (staged in shared memory), and then 3 FMAs plus one compare per
-//     covered pixel-slot: exp(-(dx^2+dy^2)/sigma^2) = w_x * w_y (Eq. 2 is
-//     separable), and the clip test dx^2 <= r^2 - dy^2 keeps the disc exact;
-//   - the warps' register tiles are then added into the shared tile one warp
-//     at a time (a fixed order), and the tile is written once, coalesced.
+//     of a shared-memory copy of the tile; lanes of a warp that hit the same
+//     pixel are summed with warp shuffles first;
+//   - small particles (r_sml < r <= r_small): one warp per particle spreads
+//     the particle's pixel box over its lanes, into shared memory;
+//   - medium and large particles are taken in batches (the chunks of n_p
+//     particles of Sec. 4.2): the CTA first tabulates, per particle, the
+//     column weights w_x(i) = exp(-dx^2/sigma^2) and the row terms
+//     e * w_y(j) (Eq. 2 is separable: exp(-(dx^2+dy^2)/sigma^2) = w_x w_y),
+//     then every warp whose row band the particle reaches adds
+//     e * w_y * w_x into its registers: three FMAs per pixel, plus a clip
+//     test folded into one saturating add on the FMA pipe (see below);
+//   - finally each thread adds the shared-memory part to its registers and
+//     writes its pixels once.
 // The large pass (r > r_large, Sec. 4.3) runs after the tile pass with the
-// same warp-register scheme over the tiles that large particles reach, and
-// adds its tile into the image (one CTA per tile, stream-ordered after the
-// tile pass, so again no atomics).
+// same scheme over segments of the tiles' large lists and adds its partial
+// tiles into the image.
+//
+// Clip (Eq. 2: zero beyond chi*sigma).  With B = 2^20 / r^2 the tables hold
+// dx^2 * B per column and (r^2 - dy^2) * B + 1 per row; the clip factor is
+// m = saturate((r^2 - dy^2) B + 1 - dx^2 B), which is exactly 1 inside the
+// disc and exactly 0 outside it, except for pixels whose distance lies within
+// r * (1 + 5e-7) -- inside the band where FP32 and FP64 may legitimately
+// disagree on an inclusive clip test anyway.
 #include "spl_geom.cuh"
 
 namespace spl {
 
 template <int T>
-struct TileShape {
-    static constexpr int RPL = T * T / 32;   // rows held by one lane
-    static constexpr int GROUPS = 32 / T;    // lane groups (rows split between them)
-    static constexpr int CHUNK = 4;          // rows per guarded chunk
-    static constexpr int NCHUNK = RPL / CHUNK;
+struct Shape {
+    static constexpr int TC = T < 32 ? T : 32;     // distinct columns per warp instruction
+    static constexpr int G = 32 / TC;              // lane groups (rows split between them)
+    static constexpr int CPL = T / TC;             // columns per lane
+    static constexpr int RPW = T / 8;              // rows per warp (8 warps)
+    static constexpr int RPL = RPW / G;            // rows per lane
+    static constexpr int P = 32;                   // particles per tabulated batch
+    static constexpr int PER = T / 8;              // table columns (and rows) per thread
 };
 
-// One medium/large particle into a warp's register tile.
-template <int T>
-__device__ __forceinline__ void warp_splat(const FrameConst &fc, float4 r0, float4 r1, int x0,
-                                           int y0, float4 *rowbuf, float *ar, float *ag, float *ab,
-                                           int lane) {
-    using S = TileShape<T>;
-    const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
-    const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;   // pixel-centre offsets
-    const float kq = r0.w, r2 = r1.x;
-    // column weight of this lane
-    const int col = lane % T, grp = lane / T;
-    const float dx = (float)(x0 + col - xi) + xh;
-    const float dx2 = dx * dx;
-    const float wx = ex2_neg(kq * dx2);
-    // row weights: lane l < T computes row l of the tile
-    __syncwarp();
-    if (lane < T) {
-        const float dy = (float)(y0 + lane - yi) + yh;
-        const float dy2 = dy * dy;
-        const float wy = ex2_neg(kq * dy2);
-        rowbuf[lane] = make_float4(r1.y * wy, r1.z * wy, r1.w * wy, r2 - dy2);
-    }
-    __syncwarp();
-    // rows the disc can reach (conservative; the exact test is dx2 <= rem)
-    const float r = sqrtf(r2) + 1e-3f;
-    const int jlo = yi - y0 + (int)ceilf(fmaxf(r0.z - 0.5f - r, -1e6f));
-    const int jhi = yi - y0 + (int)floorf(fminf(r0.z - 0.5f + r, 1e6f));
-    const int rbase = grp * S::RPL;
-#pragma unroll
-    for (int c = 0; c < S::NCHUNK; ++c) {
-        const int ra = rbase + c * S::CHUNK;
-        if (ra + S::CHUNK - 1 < jlo || ra > jhi) continue;
-#pragma unroll
-        for (int q = 0; q < S::CHUNK; ++q) {
-            const int k = c * S::CHUNK + q;
-            const float4 v = rowbuf[ra + q];
-            if (dx2 <= v.w) {
-                ar[k] = fmaf(v.x, wx, ar[k]);
-                ag[k] = fmaf(v.y, wx, ag[k]);
-                ab[k] = fmaf(v.z, wx, ab[k]);
-            }
-        }
-    }
-}
 
-// One small particle (one thread) into the shared tile.
+// One small particle into the shared tile: the warp spreads the particle's
+// pixel box (inside the tile) over its lanes, so no two lanes of a warp touch
+// the same pixel; different warps meet only through shared-memory atomics.
 template <int T>
-__device__ __forceinline__ void thread_splat(const FrameConst &fc, float4 r0, float4 r1, int x0,
-                                             int y0, float (*sacc)[T][T]) {
+__device__ __forceinline__ void warp_small(const FrameConst &fc, float4 r0, float4 r1, int x0,
+                                           int y0, float (*sacc)[T][T], int lane) {
     PixBox b;
     if (!splat_box(fc, r0, r1.x, b)) return;
     const int i0 = max(b.i0, x0), i1 = min(b.i1, x0 + T - 1);
     const int j0 = max(b.j0, y0), j1 = min(b.j1, y0 + T - 1);
+    if (i0 > i1 || j0 > j1) return;
     const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
     const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
     const float kq = r0.w, r2 = r1.x;
-    for (int j = j0; j <= j1; ++j) {
-        const float dy = (float)(j - yi) + yh;
-        const float rem = r2 - dy * dy;
-        if (rem < 0.f) continue;
-        const float wy = ex2_neg(kq * dy * dy);
-        for (int i = i0; i <= i1; ++i) {
-            const float dx = (float)(i - xi) + xh;
-            const float dx2 = dx * dx;
-            if (dx2 <= rem) {
-                const float w = wy * ex2_neg(kq * dx2);
-                atomicAdd(&sacc[0][j - y0][i - x0], r1.y * w);
-                atomicAdd(&sacc[1][j - y0][i - x0], r1.z * w);
-                atomicAdd(&sacc[2][j - y0][i - x0], r1.w * w);
-            }
+    const int bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
+    const float inv_bw = 1.f / (float)bw;
+    for (int q = lane; q < npx; q += 32) {
+        int jj = (int)(((float)q + 0.5f) * inv_bw);
+        int ii = q - jj * bw;
+        const int i = i0 + ii, j = j0 + jj;
+        const float dx = (float)(i - xi) + xh, dy = (float)(j - yi) + yh;
+        const float d2 = dx * dx + dy * dy;
+        if (d2 <= r2) {
+            const float w = ex2_neg(kq * d2);
+            atomicAdd(&sacc[0][j - y0][i - x0], r1.y * w);
+            atomicAdd(&sacc[1][j - y0][i - x0], r1.z * w);
+            atomicAdd(&sacc[2][j - y0][i - x0], r1.w * w);
         }
     }
 }
 
-// LARGE = false: tile pass (points, small, medium; writes every tile).
-// LARGE = true:  large pass (adds into tiles that have large entries).
+// Points of one warp's 32 staged records: lanes that hit the same pixel are
+// summed inside the warp first (match + shuffles), then one lane adds.
+template <int T>
+__device__ __forceinline__ void warp_points(const TileArgs &a, const float4 *s0, const float4 *s1,
+                                            int cnt, int x0, int y0, float (*sacc)[T][T], int lane) {
+    int key = -1;
+    float er = 0.f, eg = 0.f, eb = 0.f;
+    int i = 0, j = 0;
+    if (lane < cnt) {
+        const float4 r0 = s0[lane];
+        const float4 r1 = s1[lane];
+        i = unpack_xi(r0.x) - x0;
+        j = unpack_yi(r0.x) - y0;
+        if ((unsigned)i < (unsigned)T && (unsigned)j < (unsigned)T) {
+            key = j * T + i;
+            er = r1.y; eg = r1.z; eb = r1.w;
+        } else {
+            atomicOr(&a.st->err, ERR_INDEX);
+        }
+    }
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    if (__any_sync(0xffffffffu, key >= 0 && __popc(m) > 1)) {
+        float sr = 0.f, sg = 0.f, sb = 0.f;
+        for (int q = 0; q < 32; ++q) {
+            const float vr = __shfl_sync(0xffffffffu, er, q);
+            const float vg = __shfl_sync(0xffffffffu, eg, q);
+            const float vb = __shfl_sync(0xffffffffu, eb, q);
+            if ((m >> q) & 1u) { sr += vr; sg += vg; sb += vb; }
+        }
+        er = sr; eg = sg; eb = sb;
+    }
+    if (key >= 0 && lane == __ffs(m) - 1) {
+        atomicAdd(&sacc[0][j][i], er);
+        atomicAdd(&sacc[1][j][i], eg);
+        atomicAdd(&sacc[2][j][i], eb);
+    }
+}
+
+// Tabulate the separable factors of a batch of cnt <= 32 staged particles:
+// swx[p][c] = (w_x, dx^2 B) for tile column c, srow[p][j] = (e w_y, (r^2 -
+// dy^2) B + 1) for tile row j.  Thread (p, q) = (tid / 8, tid % 8) fills
+// columns and rows [q T/8, (q+1) T/8) of particle p, and decides for row
+// band q whether the disc reaches it (bit p of band_mask[q]) and whether it
+// covers the whole band (bit p of full_mask[q]).
+template <int T>
+__device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, int cnt, int x0,
+                                         int y0, float2 (*swx)[T], float4 (*srow)[T],
+                                         unsigned *band_mask, unsigned *full_mask, int tid) {
+    using S = Shape<T>;
+    const int p = tid >> 3, q = tid & 7;
+    if (p >= cnt) return;
+    const float4 r0 = st0[p], r1 = st1[p];
+    const float kq = r0.w, r2 = r1.x;
+    const float B = 1048576.f / r2;
+    const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
+    const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
+#pragma unroll
+    for (int u = 0; u < S::PER; ++u) {
+        const int k = q * S::PER + u;
+        const float dx = (float)(x0 + k - xi) + xh;
+        const float dx2 = dx * dx;
+        swx[p][k] = make_float2(ex2_neg(kq * dx2), dx2 * B);
+        const float dy = (float)(y0 + k - yi) + yh;
+        const float dy2 = dy * dy;
+        const float wy = ex2_neg(kq * dy2);
+        srow[p][k] = make_float4(r1.y * wy, r1.z * wy, r1.w * wy, fmaf(r2 - dy2, B, 1.f));
+    }
+    // row band q = rows [q RPW, (q+1) RPW) of the tile (the rows of warp q)
+    const float r = sqrtf(r2) + 1e-3f;
+    const int jlo = yi - y0 + (int)ceilf(fmaxf(r0.z - 0.5f - r, -1e6f));
+    const int jhi = yi - y0 + (int)floorf(fminf(r0.z - 0.5f + r, 1e6f));
+    const int b0 = q * S::RPW, b1 = b0 + S::RPW - 1;
+    if (jhi >= b0 && jlo <= b1) {
+        atomicOr(&band_mask[q], 1u << p);
+        const float dxa = (float)(x0 - xi) + xh, dxb = (float)(x0 + T - 1 - xi) + xh;
+        const float dya = (float)(y0 + b0 - yi) + yh, dyb = (float)(y0 + b1 - yi) + yh;
+        if (fmaxf(dya * dya, dyb * dyb) + fmaxf(dxa * dxa, dxb * dxb) <= r2 * (1.f - 4e-6f))
+            atomicOr(&full_mask[q], 1u << p);
+    }
+}
+
+// Add tabulated particle p into the registers of this thread's pixels.
+template <int T, bool FULL>
+__device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp, int col, int row0,
+                                           float (&acc)[Shape<T>::RPL][Shape<T>::CPL][3]) {
+    using S = Shape<T>;
+    float wx[S::CPL], dxb[S::CPL];
+#pragma unroll
+    for (int k = 0; k < S::CPL; ++k) {
+        const float2 v = wxp[col + 32 * k];
+        wx[k] = v.x;
+        dxb[k] = v.y;
+    }
+#pragma unroll
+    for (int q = 0; q < S::RPL; ++q) {
+        const float4 rv = rowp[row0 + q];
+#pragma unroll
+        for (int k = 0; k < S::CPL; ++k) {
+            // clip factor: exactly 1 inside the disc, 0 outside (see the top)
+            const float wk = FULL ? wx[k] : wx[k] * __saturatef(rv.w - dxb[k]);
+            acc[q][k][0] = fmaf(rv.x, wk, acc[q][k][0]);
+            acc[q][k][1] = fmaf(rv.y, wk, acc[q][k][1]);
+            acc[q][k][2] = fmaf(rv.z, wk, acc[q][k][2]);
+        }
+    }
+}
+
+// Dynamic shared memory of one CTA (bytes), in this order: srow, st0, st1,
+// swx, sacc.
+template <int T>
+constexpr size_t smem_bytes() {
+    using S = Shape<T>;
+    return sizeof(float4) * (S::P * T + 2 * kTileThreads) + sizeof(float2) * S::P * T +
+           sizeof(float) * 3 * T * T;
+}
+
+template <int T>
+constexpr int min_ctas() { return T >= 64 ? 2 : 4; }
+
+// Persistent pass over work items [item0, item0 + n_items).
 template <int T, bool LARGE>
-__global__ void __launch_bounds__(kTileThreads) tile_kernel(FrameConst fc, TileArgs a) {
-    using S = TileShape<T>;
-    __shared__ float sacc[3][T][T];
-    __shared__ float4 rowbuf[kTileThreads / 32][T];
-    const int tile = blockIdx.x;
-    const int tx = tile % fc.ntx, ty = tile / fc.ntx;
-    const int x0 = tx * fc.tile, y0 = ty * fc.tile;
+__global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(FrameConst fc, TileArgs a,
+                                                                           int item0, int n_items) {
+    using S = Shape<T>;
+    constexpr int NW = kTileThreads / 32;
+    extern __shared__ float4 smem_raw[];
+    float4 (*srow)[T] = reinterpret_cast<float4 (*)[T]>(smem_raw);
+    float4 *st0 = smem_raw + S::P * T;
+    float4 *st1 = st0 + kTileThreads;
+    float2 (*swx)[T] = reinterpret_cast<float2 (*)[T]>(st1 + kTileThreads);
+    float (*sacc)[T][T] = reinterpret_cast<float (*)[T][T]>(&swx[S::P][0]);
+    __shared__ unsigned band_mask[NW], full_mask[NW];
+    __shared__ int s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int *off = a.offsets;
     const int nt = fc.ntiles;
-    const int med_list = LARGE ? L_LARGE : L_MEDIUM;
-    const int m0 = off[med_list * nt + tile], m1 = off[med_list * nt + tile + 1];
-    if (LARGE && m0 == m1) return;
-
-    for (int k = tid; k < 3 * T * T; k += kTileThreads) (&sacc[0][0][0])[k] = 0.f;
-    __syncthreads();
-
-    if (!LARGE) {
-        // points (Sec. 4.1): one pixel each
-        const int p0 = off[L_POINT * nt + tile], p1 = off[L_POINT * nt + tile + 1];
-        for (int k = p0 + tid; k < p1; k += kTileThreads) {
-            const unsigned id = a.entries[k];
-            const float4 r0 = a.rec0[id];
-            const float4 r1 = a.rec1[id];
-            const int i = unpack_xi(r0.x) - x0, j = unpack_yi(r0.x) - y0;
-            if ((unsigned)i < (unsigned)T && (unsigned)j < (unsigned)T) {
-                atomicAdd(&sacc[0][j][i], r1.y);
-                atomicAdd(&sacc[1][j][i], r1.z);
-                atomicAdd(&sacc[2][j][i], r1.w);
-            } else {
-                atomicOr(&a.st->err, ERR_INDEX);
-            }
-        }
-        // small particles: one thread each
-        const int s0 = off[L_SMALL * nt + tile], s1 = off[L_SMALL * nt + tile + 1];
-        for (int k = s0 + tid; k < s1; k += kTileThreads) {
-            const unsigned id = a.entries[k];
-            thread_splat<T>(fc, a.rec0[id], a.rec1[id], x0, y0, sacc);
-        }
-    }
-
-    // medium (or large) particles: one warp each, private register tiles
-    float ar[S::RPL], ag[S::RPL], ab[S::RPL];
-#pragma unroll
-    for (int k = 0; k < S::RPL; ++k) ar[k] = ag[k] = ab[k] = 0.f;
-    const bool busy = m0 + warp < m1;
-    for (int k = m0 + warp; k < m1; k += kTileThreads / 32) {
-        const unsigned id = a.entries[k];
-        warp_splat<T>(fc, a.rec0[id], a.rec1[id], x0, y0, rowbuf[warp], ar, ag, ab, lane);
-    }
-    // add the register tiles into the shared tile, one warp after another
-    const int col = lane % T, rbase = (lane / T) * S::RPL;
-    for (int w = 0; w < kTileThreads / 32; ++w) {
+    int *counter = &a.st->item_counter[LARGE ? 1 : 0];
+    for (;;) {
         __syncthreads();
-        if (w == warp && busy) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        for (int k = tid; k < 3 * T * T; k += kTileThreads) (&sacc[0][0][0])[k] = 0.f;
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const WorkItem w = a.items[item0 + it];
+        const int tile = w.tile;
+        const int x0 = (tile % fc.ntx) * T, y0 = (tile / fc.ntx) * T;
+        int lb0 = 0, le0 = 0, lb1 = 0, le1 = 0, lb2 = 0, le2 = 0;
+        if (w.list < 0) {
+            lb0 = a.offsets[L_POINT * nt + tile]; le0 = a.offsets[L_POINT * nt + tile + 1];
+            lb1 = a.offsets[L_SMALL * nt + tile]; le1 = a.offsets[L_SMALL * nt + tile + 1];
+            lb2 = a.offsets[L_MEDIUM * nt + tile]; le2 = a.offsets[L_MEDIUM * nt + tile + 1];
+        } else if (w.list == L_POINT) {
+            lb0 = w.start; le0 = w.end;
+        } else if (w.list == L_SMALL) {
+            lb1 = w.start; le1 = w.end;
+        } else {
+            lb2 = w.start; le2 = w.end;      // medium (tile pass) or large (large pass)
+        }
+        const int col = lane % S::TC, row0 = warp * S::RPW + (lane / S::TC) * S::RPL;
+        float acc[S::RPL][S::CPL][3];
 #pragma unroll
-            for (int k = 0; k < S::RPL; ++k) {
-                sacc[0][rbase + k][col] += ar[k];
-                sacc[1][rbase + k][col] += ag[k];
-                sacc[2][rbase + k][col] += ab[k];
+        for (int q = 0; q < S::RPL; ++q)
+#pragma unroll
+            for (int k = 0; k < S::CPL; ++k) acc[q][k][0] = acc[q][k][1] = acc[q][k][2] = 0.f;
+
+        // points (Sec. 4.1): batches of 256 staged records, warp-aggregated
+#pragma unroll 1
+        for (int base = lb0; base < le0; base += kTileThreads) {
+            const int cnt = min(kTileThreads, le0 - base);
+            if (tid < cnt) {
+                const unsigned id = a.entries[base + tid];
+                st0[tid] = a.rec0[id];
+                st1[tid] = a.rec1[id];
+            }
+            __syncthreads();
+            warp_points<T>(a, st0 + warp * 32, st1 + warp * 32, cnt - warp * 32, x0, y0, sacc, lane);
+            __syncthreads();
+        }
+        // small particles: one warp each over the pixel box
+#pragma unroll 1
+        for (int base = lb1; base < le1; base += kTileThreads) {
+            const int cnt = min(kTileThreads, le1 - base);
+            if (tid < cnt) {
+                const unsigned id = a.entries[base + tid];
+                st0[tid] = a.rec0[id];
+                st1[tid] = a.rec1[id];
+            }
+            __syncthreads();
+            for (int k = warp; k < cnt; k += NW) warp_small<T>(fc, st0[k], st1[k], x0, y0, sacc, lane);
+            __syncthreads();
+        }
+        // medium (or large) particles: tabulate a batch, then every row band
+        // adds it; the next batch's records are fetched into registers while
+        // the current one is processed
+        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+        if (lb2 + tid < le2 && tid < S::P) {
+            const unsigned id = a.entries[lb2 + tid];
+            n0 = a.rec0[id];
+            n1 = a.rec1[id];
+        }
+#pragma unroll 1
+        for (int base = lb2; base < le2; base += S::P) {
+            const int cnt = min(S::P, le2 - base);
+            if (tid < cnt) {
+                st0[tid] = n0;
+                st1[tid] = n1;
+            }
+            if (tid < NW) band_mask[tid] = full_mask[tid] = 0u;
+            __syncthreads();
+            if (base + S::P + tid < le2 && tid < S::P) {
+                const unsigned id = a.entries[base + S::P + tid];
+                n0 = a.rec0[id];
+                n1 = a.rec1[id];
+            }
+            tabulate<T>(st0, st1, cnt, x0, y0, swx, srow, band_mask, full_mask, tid);
+            __syncthreads();
+            // this warp's row band: only the particles that reach it
+            unsigned mask = band_mask[warp];
+            const unsigned fullm = full_mask[warp];
+            while (mask) {
+                const int p = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                if ((fullm >> p) & 1u)
+                    band_splat<T, true>(swx[p], srow[p], col, row0, acc);
+                else
+                    band_splat<T, false>(swx[p], srow[p], col, row0, acc);
+            }
+            __syncthreads();
+        }
+
+        // write: shared part + registers, stored (only item of its tile) or added
+        const bool store = !LARGE && w.list < 0;
+#pragma unroll
+        for (int q = 0; q < S::RPL; ++q) {
+            const int row = row0 + q;
+#pragma unroll
+            for (int k = 0; k < S::CPL; ++k) {
+                const int cx = col + 32 * k;
+                if (y0 + row >= fc.height || x0 + cx >= fc.width) continue;
+                float *dst = a.image + 3 * ((int64_t)(y0 + row) * fc.width + x0 + cx);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float v = sacc[c][row][cx] + acc[q][k][c];
+                    if (store)
+                        dst[c] = v;
+                    else if (v != 0.f)
+                        atomicAdd(dst + c, v);
+                }
             }
         }
     }
-    __syncthreads();
-
-    // write (tile pass) or add (large pass) the tile, row segments contiguous
-    const int wv = min(T, fc.width - x0), hv = min(T, fc.height - y0);
-    for (int q = tid; q < 3 * T * T; q += kTileThreads) {
-        const int row = q / (3 * T), rem = q - row * 3 * T;
-        const int c = rem % 3, colq = rem / 3;
-        if (row >= hv || colq >= wv) continue;
-        float *dst = a.image + 3 * ((int64_t)(y0 + row) * fc.width + x0 + colq) + c;
-        const float v = sacc[c][row][colq];
-        if (LARGE)
-            *dst += v;
-        else
-            *dst = v;
-    }
 }
 
-void launch_tile_pass(const FrameConst &fc, const TileArgs &a, cudaStream_t s) {
-    if (fc.tile == 16)
-        tile_kernel<16, false><<<fc.ntiles, kTileThreads, 0, s>>>(fc, a);
-    else
-        tile_kernel<32, false><<<fc.ntiles, kTileThreads, 0, s>>>(fc, a);
+template <int T, bool LARGE>
+static void launch_items_t(const FrameConst &fc, const TileArgs &a, int item0, int n_items, int sms,
+                           cudaStream_t s) {
+    constexpr size_t bytes = smem_bytes<T>();
+    cudaFuncSetAttribute(item_kernel<T, LARGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
+    const int cap = sms * min_ctas<T>();
+    const int g = n_items < cap ? n_items : cap;
+    item_kernel<T, LARGE><<<g, kTileThreads, bytes, s>>>(fc, a, item0, n_items);
 }
 
-void launch_large_pass(const FrameConst &fc, const TileArgs &a, cudaStream_t s) {
+template <bool LARGE>
+static void launch_items(const FrameConst &fc, const TileArgs &a, int item0, int n_items, int sms,
+                         cudaStream_t s) {
+    if (n_items <= 0) return;
     if (fc.tile == 16)
-        tile_kernel<16, true><<<fc.ntiles, kTileThreads, 0, s>>>(fc, a);
+        launch_items_t<16, LARGE>(fc, a, item0, n_items, sms, s);
+    else if (fc.tile == 64)
+        launch_items_t<64, LARGE>(fc, a, item0, n_items, sms, s);
     else
-        tile_kernel<32, true><<<fc.ntiles, kTileThreads, 0, s>>>(fc, a);
+        launch_items_t<32, LARGE>(fc, a, item0, n_items, sms, s);
+}
+
+void launch_tile_pass(const FrameConst &fc, const TileArgs &a, int n_items, int sms, cudaStream_t s) {
+    launch_items<false>(fc, a, 0, n_items, sms, s);
+}
+
+void launch_large_pass(const FrameConst &fc, const TileArgs &a, int item0, int n_items, int sms,
+                       cudaStream_t s) {
+    launch_items<true>(fc, a, item0, n_items, sms, s);
 }
 
 // E_p = A_p solution of Eq. 1 applied to the additive sum: I = 1 - exp(-S).

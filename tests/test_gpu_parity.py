@@ -134,7 +134,7 @@ def test_random_scenes_ragged_sizes(rnd, torch_cuda, seed, w, h):
     check_image(rnd, torch_cuda, p, scenes.ramp_palette(), cam)
 
 
-@pytest.mark.parametrize("tile", [16, 32])
+@pytest.mark.parametrize("tile", [16, 32, 64])
 @pytest.mark.parametrize("r_small,r_large", [(0.5, 0.5), (4.0, 64.0), (1e6, 1e6), (2.0, 8.0)])
 def test_thresholds_and_tile_size_do_not_change_the_image(rnd, torch_cuda, tile, r_small, r_large):
     # r_small / r_large / tile only choose how a particle is processed
