@@ -124,9 +124,10 @@ __device__ __forceinline__ void warp_points(const TileArgs &a, const float4 *s0,
 // Tabulate the separable factors of a batch of cnt <= 32 staged particles:
 // swx[p][c] = (w_x, dx^2 B) for tile column c, srow[p][j] = (e w_y, (r^2 -
 // dy^2) B + 1) for tile row j.  Thread (p, q) = (tid / 8, tid % 8) fills
-// columns and rows [q T/8, (q+1) T/8) of particle p, and decides for row
-// band q whether the disc reaches it (bit p of band_mask[q]) and whether it
-// covers the whole band (bit p of full_mask[q]).
+// columns and rows q, q + 8, q + 16, ... of particle p (consecutive lanes
+// write consecutive table entries, free of bank conflicts), and decides for
+// row band q whether the disc reaches it (bit p of band_mask[q]) and whether
+// it covers the whole band (bit p of full_mask[q]).
 template <int T>
 __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, int cnt, int x0,
                                          int y0, float2 (*swx)[T], float4 (*srow)[T],
@@ -141,7 +142,7 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
     const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
 #pragma unroll
     for (int u = 0; u < S::PER; ++u) {
-        const int k = q * S::PER + u;
+        const int k = q + 8 * u;
         const float dx = (float)(x0 + k - xi) + xh;
         const float dx2 = dx * dx;
         swx[p][k] = make_float2(ex2_neg(kq * dx2), dx2 * B);
@@ -200,7 +201,7 @@ constexpr size_t smem_bytes() {
 }
 
 template <int T>
-constexpr int min_ctas() { return T >= 64 ? 2 : 4; }
+constexpr int min_ctas() { return T >= 64 ? 2 : (T == 32 ? 5 : 4); }
 
 // Persistent pass over work items [item0, item0 + n_items).
 template <int T, bool LARGE>
