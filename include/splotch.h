@@ -48,6 +48,7 @@ extern "C" {
 #define SPL_ECUDA 3     /* CUDA runtime error */
 #define SPL_ESTATE 4    /* call out of order (e.g. render before particles) */
 #define SPL_EDEVICE 5   /* a device-side check failed during the last render */
+#define SPL_ELIMIT 6    /* a size beyond the fixed scratch of spl_render_noalloc */
 
 /* memory space of caller buffers */
 #define SPL_MEM_HOST 0
@@ -175,6 +176,36 @@ int spl_count_work(spl_ctx *ctx, int64_t out[4]);
  * emission e (n*3), class (-2 inactive, 0 point, 1 small, 2 medium, 3 large). */
 int spl_get_records(spl_ctx *ctx, int64_t n, double *xs, double *ys, float *r,
                     float *e, int32_t *cls);
+
+/* Render without allocating: for callers that cannot call cudaMalloc (code
+ * running where device allocation is forbidden or must stay with the
+ * caller: inside a graph capture that must not create allocations, under a
+ * memory budget the caller owns, or in a host application that passes only
+ * its own buffers).  It needs no context.  It runs the kernels of
+ * spl_render, with every scratch buffer carved from one file-scope
+ * __device__ array of about 15 MiB that each GPU loading the library holds
+ * until the process exits.  The paper has no counterpart: it is a property
+ * of this library, not of the method.
+ *   p       particles in DEVICE memory (mem_space must be SPL_MEM_DEVICE),
+ *           n <= 131072;
+ *   cam     camera with ceil(width/tile) * ceil(height/tile) <= 16384 tiles;
+ *   q       parameters, or NULL for spl_default_params();
+ *   rgb     colour map (HOST memory, npal RGB triples, 1 <= npal <= 1024)
+ *           looked up over [s_min, s_max];
+ *   d_image DEVICE output, width*height*3 FP32, fully overwritten;
+ *   device  CUDA ordinal; stream: cudaStream_t or NULL.
+ * Sizes beyond those limits, or a frame whose tile lists exceed 2^21
+ * entries or 32768 work items, return SPL_ELIMIT and render nothing.  The
+ * first call on a device looks up the array's device address (with that
+ * device made current); make that first call before any stream capture.
+ * The call synchronises the stream once (after binning) and returns with the
+ * remaining kernels queued.  Every call shares the one array, which keeps
+ * the last call's contents (each call clears what must start at zero), so
+ * calls whose kernels overlap on the GPU -- on different streams, or from
+ * different threads -- race and corrupt each other: serialise them. */
+int spl_render_noalloc(const spl_particles *p, const spl_camera *cam, const spl_params *q,
+                       const float *rgb, int32_t npal, float s_min, float s_max, float *d_image,
+                       int32_t device, void *stream);
 
 const char *spl_error_string(int code);
 

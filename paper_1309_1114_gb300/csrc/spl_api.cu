@@ -110,6 +110,7 @@ extern "C" const char *spl_error_string(int code) {
         case SPL_ECUDA: return "CUDA error";
         case SPL_ESTATE: return "call out of order";
         case SPL_EDEVICE: return "device-side check failed";
+        case SPL_ELIMIT: return "size beyond the fixed scratch of spl_render_noalloc";
         default: return "unknown status";
     }
 }
@@ -596,4 +597,166 @@ extern "C" int spl_count_work(spl_ctx *c, int64_t out[4]) {
     }
     work.release();
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// spl_render_noalloc: the render for callers that cannot allocate device
+// memory -- code that runs where cudaMalloc is not allowed or not wanted
+// (inside a CUDA-graph capture that must not create allocations, under a
+// memory budget owned by someone else, or in a host application that hands
+// us only its own buffers).  The same kernels as spl_render run, but every
+// scratch buffer is carved from the file-scope device array below, whose
+// size is fixed when the library is loaded; every GPU that loads the library
+// keeps it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kNaMaxParticles = 131072;
+constexpr int kNaMaxTiles = 16384;
+constexpr int64_t kNaMaxEntries = 2097152;
+constexpr int kNaMaxItems = 32768;
+
+constexpr size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t kNaStats = 0;
+constexpr size_t kNaPal = kNaStats + na_round(sizeof(DevStats));
+constexpr size_t kNaRec0 = kNaPal + na_round(sizeof(float) * 3 * kMaxPalette);
+constexpr size_t kNaRec1 = kNaRec0 + na_round(sizeof(float4) * kNaMaxParticles);
+constexpr size_t kNaLarge = kNaRec1 + na_round(sizeof(float4) * kNaMaxParticles);
+constexpr size_t kNaCounts = kNaLarge + na_round(sizeof(unsigned) * kNaMaxParticles);
+constexpr size_t kNaOffsets = kNaCounts + na_round(sizeof(int) * NLIST * kNaMaxTiles);
+constexpr size_t kNaCursor = kNaOffsets + na_round(sizeof(int) * (NLIST * kNaMaxTiles + 1));
+constexpr size_t kNaItemCounts = kNaCursor + na_round(sizeof(int) * NLIST * kNaMaxTiles);
+constexpr size_t kNaItemOffsets = kNaItemCounts + na_round(sizeof(int) * 2 * kNaMaxTiles);
+constexpr size_t kNaEntries = kNaItemOffsets + na_round(sizeof(int) * (2 * kNaMaxTiles + 1));
+constexpr size_t kNaItems = kNaEntries + na_round(sizeof(unsigned) * kNaMaxEntries);
+constexpr size_t kNaBytes = kNaItems + na_round(sizeof(WorkItem) * kNaMaxItems);
+}  // namespace
+
+// The scratch itself (about 15 MiB).  In host code this name is only a
+// host-side stand-in; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char spl_noalloc_scratch[kNaBytes];
+
+namespace {
+constexpr int kNaMaxDevices = 64;
+unsigned char *g_na_scratch[kNaMaxDevices] = {};
+
+// Device address of the scratch on `device` (which must be current); looked
+// up on the first call for that device.
+int na_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= kNaMaxDevices) return SPL_EINVAL;
+    if (!g_na_scratch[device]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, spl_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return SPL_ECUDA;
+        }
+        g_na_scratch[device] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_na_scratch[device];
+    return SPL_OK;
+}
+}  // namespace
+
+extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
+                                  const spl_params *q, const float *rgb, int32_t npal, float s_min,
+                                  float s_max, float *d_image, int32_t device, void *stream) {
+    if (!p || !cam || !rgb || !d_image || p->n < 0) return SPL_EINVAL;
+    if (p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
+    if (p->attr_type != SPL_ATTR_F32 && p->attr_type != SPL_ATTR_F16) return SPL_EINVAL;
+    if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
+    if (!camera_ok(cam)) return SPL_EINVAL;
+    if (npal < 1 || npal > kMaxPalette || !std::isfinite(s_min) || !std::isfinite(s_max))
+        return SPL_EINVAL;
+    for (int k = 0; k < 3 * npal; ++k)
+        if (!std::isfinite(rgb[k])) return SPL_EINVAL;
+    spl_ctx tmp;   // parameters only; none of its buffers is allocated
+    if (q) {
+        if (!params_ok(q)) return SPL_EINVAL;
+        tmp.par = *q;
+    } else {
+        spl_default_params(&tmp.par);
+    }
+    tmp.npal = npal;
+    tmp.s_min = s_min;
+    tmp.s_max = s_max;
+    const FrameConst fc = make_frame(&tmp, *cam);
+    if (p->n > kNaMaxParticles || fc.ntiles > kNaMaxTiles) return SPL_ELIMIT;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return SPL_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return SPL_EINVAL;
+    DeviceGuard g(device);
+    unsigned char *base = nullptr;
+    SPL_TRY(na_scratch(device, &base));
+    DevStats *dst = reinterpret_cast<DevStats *>(base + kNaStats);
+    float *pal = reinterpret_cast<float *>(base + kNaPal);
+    float4 *rec0 = reinterpret_cast<float4 *>(base + kNaRec0);
+    float4 *rec1 = reinterpret_cast<float4 *>(base + kNaRec1);
+    unsigned *large_ids = reinterpret_cast<unsigned *>(base + kNaLarge);
+    int *counts = reinterpret_cast<int *>(base + kNaCounts);
+    int *offsets = reinterpret_cast<int *>(base + kNaOffsets);
+    int *cursor = reinterpret_cast<int *>(base + kNaCursor);
+    int *item_counts = reinterpret_cast<int *>(base + kNaItemCounts);
+    int *item_offsets = reinterpret_cast<int *>(base + kNaItemOffsets);
+    unsigned *entries = reinterpret_cast<unsigned *>(base + kNaEntries);
+    WorkItem *items = reinterpret_cast<WorkItem *>(base + kNaItems);
+    cudaStream_t s = (cudaStream_t)stream;
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+
+    // the array keeps the previous call's contents: clear what starts at zero
+    SPL_CUDA(cudaMemcpyAsync(pal, rgb, sizeof(float) * 3 * npal, cudaMemcpyHostToDevice, s));
+    SPL_CUDA(cudaMemsetAsync(dst, 0, sizeof(DevStats), s));
+    SPL_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * NLIST * fc.ntiles, s));
+    RasterArgs ra{};
+    ra.n = p->n;
+    ra.x = p->x; ra.y = p->y; ra.z = p->z;
+    ra.h = p->h; ra.I = p->I; ra.s = p->s;
+    ra.pal = pal;
+    ra.rec0 = rec0; ra.rec1 = rec1;
+    ra.counts = counts;
+    ra.large_ids = large_ids;
+    ra.st = dst;
+    launch_raster(fc, ra, p->attr_type == SPL_ATTR_F16, sms, s);
+    BinArgs ba{};
+    ba.n = p->n;
+    ba.rec0 = rec0; ba.rec1 = rec1;
+    ba.large_ids = large_ids;
+    ba.counts = counts;
+    ba.cursor = cursor;
+    ba.st = dst;
+    launch_count_large(fc, ba, sms, s);
+    launch_scan(NLIST * fc.ntiles, counts, offsets, cursor, NLIST, dst->totals, s);
+    launch_item_counts(fc, offsets, item_counts, s);
+    launch_scan(2 * fc.ntiles, item_counts, item_offsets, nullptr, 2, dst->item_totals, s);
+    SPL_CUDA(cudaGetLastError());
+    DevStats h;
+    SPL_CUDA(cudaMemcpyAsync(&h, dst, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    SPL_CUDA(cudaStreamSynchronize(s));
+    if (h.err) return SPL_EDEVICE;
+    int64_t total = 0;
+    for (int k = 0; k < NLIST; ++k) total += h.totals[k];
+    const int n_tile_items = h.item_totals[0], n_large_items = h.item_totals[1];
+    if (total > kNaMaxEntries || (int64_t)n_tile_items + n_large_items > kNaMaxItems)
+        return SPL_ELIMIT;
+    SPL_CUDA(cudaMemsetAsync(d_image, 0, sizeof(float) * 3 * (size_t)cam->width * cam->height, s));
+    ba.entries = entries;
+    ba.entries_cap = kNaMaxEntries;
+    launch_scatter(fc, ba, sms, s);
+    launch_fill_items(fc, offsets, item_offsets, items, s);
+    TileArgs ta{};
+    ta.rec0 = rec0; ta.rec1 = rec1;
+    ta.offsets = offsets;
+    ta.entries = entries;
+    ta.items = items;
+    ta.image = d_image;
+    ta.st = dst;
+    launch_tile_pass(fc, ta, n_tile_items, sms, s);
+    launch_large_pass(fc, ta, n_tile_items, n_large_items, sms, s);
+    if (tmp.par.mode == SPL_MODE_EA)
+        launch_epilogue_ea(d_image, (int64_t)3 * cam->width * cam->height, sms, s);
+    SPL_CUDA(cudaGetLastError());
+    return SPL_OK;
 }

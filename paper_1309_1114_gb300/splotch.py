@@ -16,7 +16,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libsplotch.so")
 
-SPL_OK, SPL_EINVAL, SPL_ENOMEM, SPL_ECUDA, SPL_ESTATE, SPL_EDEVICE = range(6)
+SPL_OK, SPL_EINVAL, SPL_ENOMEM, SPL_ECUDA, SPL_ESTATE, SPL_EDEVICE, SPL_ELIMIT = range(7)
 SPL_MEM_HOST, SPL_MEM_DEVICE = 0, 1
 SPL_ATTR_F32, SPL_ATTR_F16 = 0, 1
 SPL_MODE_ADDITIVE, SPL_MODE_EA = 0, 1
@@ -74,6 +74,8 @@ _SIGS = {
     "spl_set_timing": [_P, C.c_int32],
     "spl_get_records": [_P, C.c_int64, _P, _P, _P, _P, _P],
     "spl_count_work": [_P, C.POINTER(C.c_int64)],
+    "spl_render_noalloc": [C.POINTER(spl_particles), C.POINTER(spl_camera), C.POINTER(spl_params),
+                           _P, C.c_int32, C.c_float, C.c_float, _P, C.c_int32, _P],
     "spl_error_string": [C.c_int],
 }
 
