@@ -37,8 +37,10 @@ WORKLOADS = {
     "clustered": {"scene": "clustered", "label": "clustered-10M-1024sq-f32",
                   "desc": "10M particles, 70% in 500 Plummer haloes + 30% uniform background, "
                           "density-derived h, FP32 attributes, 1024x1024 RGB FP32"},
-    "precision": {"scene": "precision", "label": "clustered-100M-2048sq-f16attr", "fp16": True,
+    "precision": {"scene": "precision", "label": "clustered-100M-2048sq-f16attr", "fp16": "all",
                   "desc": "100M clustered particles, h/I/s stored FP16, 2048x2048 RGB FP32"},
+    "precision-mixed": {"scene": "precision", "label": "clustered-100M-2048sq-f16IS", "fp16": "is",
+                        "desc": "100M clustered particles, I/s stored FP16, h FP32, 2048x2048 RGB FP32"},
     "precision32": {"scene": "precision", "label": "clustered-100M-2048sq-f32",
                     "desc": "100M clustered particles, FP32 attributes, 2048x2048 RGB FP32"},
     "uniform": {"scene": "uniform", "label": "uniform-200k-256sq-f32",
@@ -221,7 +223,11 @@ def run_ours(args, wl):
     scene = make_scene(wl)
     cam = scene.cams[0]
     W, H = cam["width"], cam["height"]
-    fp16 = scene.fp16 if wl.get("fp16") else None
+    fp16 = None
+    if wl.get("fp16") == "all":
+        fp16 = scene.fp16
+    elif wl.get("fp16") == "is":
+        fp16 = {k: scene.fp16[k] for k in ("I", "s")}
     stream = torch.cuda.current_stream()
     r = Renderer(local, stream.cuda_stream)
     r.load(scene.parts, fp16)
@@ -271,7 +277,7 @@ def run_ours(args, wl):
     dom = "tile" if stage["tile"] >= stage["large"] else "large"
     flops = tile_flops if dom == "tile" else large_flops
     achieved = flops / (stage[dom] * 1e-3) / 1e12 if stage[dom] > 0 else 0.0
-    kname = "tile_kernel" if dom == "tile" else "tile_kernel_large"
+    kname = f"item_kernel<{st['tile_px']}, {0 if dom == 'tile' else 1}>"
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
                 "kernel": kname, "kernel_ms": stage[dom],
@@ -280,7 +286,7 @@ def run_ours(args, wl):
                 "work": {"point_deposits": work[0], "small_pairs": work[1],
                          "medium_pairs": work[2], "large_pairs": work[3],
                          "flops_per_pair": FLOPS_PER_PAIR}}
-    bytes_per_particle = 18 if fp16 is not None else 24
+    bytes_per_particle = {None: 24, "all": 18, "is": 20}[wl.get("fp16")]
     alg_bytes = scene.n * bytes_per_particle + 12 * W * H
     hbm = float(peaks.get("hbm_gbs", 6771.1))
     hbm_frac = alg_bytes / (ms * 1e-3) / (hbm * 1e9)
@@ -302,7 +308,8 @@ def run_ours(args, wl):
         if fp16 is None:
             r.load(dict(xyz, **attrs))
         else:
-            r.load(xyz, attrs)
+            r.load(dict(xyz, **{k: attrs[k] for k in attrs if k not in fp16}),
+                   {k: attrs[k] for k in fp16})
         r.render_host(host_np)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if ws > 1:
@@ -328,7 +335,7 @@ def run_ours(args, wl):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["label"], "description": wl["desc"],
                        "n_particles": scene.n, "image": [W, H],
-                       "attributes": "f16" if fp16 is not None else "f32",
+                       "attributes": {None: "f32", "all": "h,I,s f16", "is": "I,s f16; h f32"}[wl.get("fp16")],
                        "tile_px": 32, "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (particles + per-frame records > 129 MB); no flush"},
             "roofline": roofline,

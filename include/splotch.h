@@ -55,9 +55,12 @@ extern "C" {
 #define SPL_MEM_DEVICE 1
 
 /* storage type of the per-particle attributes h, I, s */
-#define SPL_ATTR_F32 0
-#define SPL_ATTR_F16 1   /* IEEE binary16; widened to FP32 on load (Sec. 3.2.3 ideal of
-                            one load per particle, half the attribute bytes) */
+#define SPL_ATTR_F32 0    /* h, I, s in FP32: 24 B per particle */
+#define SPL_ATTR_F16 1    /* h, I, s in IEEE binary16, widened to FP32 on load: 18 B per
+                             particle (the memory-access model of Sec. 3.2: one load per
+                             particle, fewer bytes).  h enters exp(-d^2/h^2), so its 2^-11
+                             rounding moves clip-edge weights by up to ~1e-2 relative */
+#define SPL_ATTR_F16_IS 2 /* h in FP32, I and s in binary16: 20 B per particle */
 
 /* output modes */
 #define SPL_MODE_ADDITIVE 0   /* image = sum of clipped Gaussians (Eq. 1, E_p = A_p, thin) */
@@ -77,7 +80,7 @@ typedef struct {
     const float *x, *y, *z;    /* positions, FP32, n each */
     const void *h, *I, *s;     /* smoothing length, intensity, colour scalar:
                                   float or binary16 according to attr_type */
-    int32_t attr_type;         /* SPL_ATTR_F32 or SPL_ATTR_F16 */
+    int32_t attr_type;         /* SPL_ATTR_F32, SPL_ATTR_F16 or SPL_ATTR_F16_IS */
     int32_t mem_space;         /* SPL_MEM_HOST or SPL_MEM_DEVICE (all six) */
 } spl_particles;
 

@@ -210,17 +210,18 @@ extern "C" int spl_destroy(spl_ctx *c) {
 
 extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
     if (!c || !p || p->n < 0) return SPL_EINVAL;
-    if (p->attr_type != SPL_ATTR_F32 && p->attr_type != SPL_ATTR_F16) return SPL_EINVAL;
+    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
     if (p->mem_space != SPL_MEM_HOST && p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
     if (p->n > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // ids are 32-bit
     DeviceGuard g(c->device);
     const size_t n = (size_t)p->n;
-    const size_t ab = p->attr_type == SPL_ATTR_F16 ? 2 : 4;
+    const size_t ah = p->attr_type == SPL_ATTR_F16 ? 2 : 4;     // bytes of h
+    const size_t ab = p->attr_type == SPL_ATTR_F32 ? 4 : 2;     // bytes of I and s
     SPL_TRY(c->x.ensure(n ? n : 1));
     SPL_TRY(c->y.ensure(n ? n : 1));
     SPL_TRY(c->z.ensure(n ? n : 1));
-    SPL_TRY(c->h.ensure((n ? n : 1) * ab));
+    SPL_TRY(c->h.ensure((n ? n : 1) * ah));
     SPL_TRY(c->I.ensure((n ? n : 1) * ab));
     SPL_TRY(c->s.ensure((n ? n : 1) * ab));
     const cudaMemcpyKind kind =
@@ -229,7 +230,7 @@ extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
         SPL_CUDA(cudaMemcpyAsync(c->x.p, p->x, n * 4, kind, c->stream));
         SPL_CUDA(cudaMemcpyAsync(c->y.p, p->y, n * 4, kind, c->stream));
         SPL_CUDA(cudaMemcpyAsync(c->z.p, p->z, n * 4, kind, c->stream));
-        SPL_CUDA(cudaMemcpyAsync(c->h.p, p->h, n * ab, kind, c->stream));
+        SPL_CUDA(cudaMemcpyAsync(c->h.p, p->h, n * ah, kind, c->stream));
         SPL_CUDA(cudaMemcpyAsync(c->I.p, p->I, n * ab, kind, c->stream));
         SPL_CUDA(cudaMemcpyAsync(c->s.p, p->s, n * ab, kind, c->stream));
     }
@@ -410,7 +411,7 @@ static int render_frame(spl_ctx *c, const spl_camera &cam, float *d_image, cudaS
     ra.counts = c->counts.p;
     ra.large_ids = c->large_ids.p;
     ra.st = c->dstats.p;
-    launch_raster(fc, ra, c->attr_type == SPL_ATTR_F16, c->sms, s);
+    launch_raster(fc, ra, c->attr_type, c->sms, s);
     record_event(c, 1, s);
     BinArgs ba{};
     ba.n = c->n;
@@ -587,7 +588,7 @@ extern "C" int spl_count_work(spl_ctx *c, int64_t out[4]) {
         ra.counts = c->counts.p;
         ra.large_ids = c->large_ids.p;
         ra.st = c->dstats.p;
-        launch_raster(fc, ra, c->attr_type == SPL_ATTR_F16, c->sms, s);
+        launch_raster(fc, ra, c->attr_type, c->sms, s);
         launch_count_work(fc, c->rec0.p, c->rec1.p, c->n, work.p, c->sms, s);
         unsigned long long h[4] = {0, 0, 0, 0};
         rc = cuda_status(cudaGetLastError());
@@ -662,7 +663,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
                                   float s_max, float *d_image, int32_t device, void *stream) {
     if (!p || !cam || !rgb || !d_image || p->n < 0) return SPL_EINVAL;
     if (p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
-    if (p->attr_type != SPL_ATTR_F32 && p->attr_type != SPL_ATTR_F16) return SPL_EINVAL;
+    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
     if (!camera_ok(cam)) return SPL_EINVAL;
     if (npal < 1 || npal > kMaxPalette || !std::isfinite(s_min) || !std::isfinite(s_max))
@@ -719,7 +720,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     ra.counts = counts;
     ra.large_ids = large_ids;
     ra.st = dst;
-    launch_raster(fc, ra, p->attr_type == SPL_ATTR_F16, sms, s);
+    launch_raster(fc, ra, p->attr_type, sms, s);
     BinArgs ba{};
     ba.n = p->n;
     ba.rec0 = rec0; ba.rec1 = rec1;

@@ -103,7 +103,7 @@ struct TileArgs {
 };
 
 // Launchers (stream-ordered, no synchronisation).
-void launch_raster(const FrameConst &fc, const RasterArgs &a, bool f16, int sms, cudaStream_t s);
+void launch_raster(const FrameConst &fc, const RasterArgs &a, int attr, int sms, cudaStream_t s);
 void launch_count_large(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s);
 // Exclusive scan of in[0..m) into out[0..m] (out[m] = total); cursor (may be
 // null) receives a copy of out[0..m); seg_totals[k] = total of the k-th of

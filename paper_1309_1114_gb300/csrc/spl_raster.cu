@@ -67,9 +67,9 @@ __device__ __forceinline__ void split_pos(df v, int &xi, float &xf) {
     if (xf < 0.f) { xf += 1.f; xi -= 1; }
 }
 
-template <bool F16>
+template <bool HALF>
 __device__ __forceinline__ float load_attr(const void *p, int64_t i) {
-    if (F16) return __half2float(static_cast<const __half *>(p)[i]);
+    if (HALF) return __half2float(static_cast<const __half *>(p)[i]);
     return static_cast<const float *>(p)[i];
 }
 
@@ -210,7 +210,9 @@ __device__ __forceinline__ void hash_clear(int *keys, int *vals) {
     }
 }
 
-template <bool F16>
+// ATTR: 0 = h, I, s in FP32; 1 = all three in binary16; 2 = h in FP32, I and s
+// in binary16.
+template <int ATTR>
 __global__ void __launch_bounds__(256) raster_kernel(FrameConst fc, RasterArgs a) {
     __shared__ float spal[3 * kMaxPalette];
     __shared__ int keys[kHash], vals[kHash];
@@ -230,8 +232,8 @@ __global__ void __launch_bounds__(256) raster_kernel(FrameConst fc, RasterArgs a
         int cls = CLS_INACTIVE;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
         if (valid) {
-            cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_attr<F16>(a.h, i),
-                             load_attr<F16>(a.I, i), load_attr<F16>(a.s, i), r0, r1);
+            cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_attr<ATTR == 1>(a.h, i),
+                             load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i), r0, r1);
             a.rec0[i] = r0;
             a.rec1[i] = r1;
         }
@@ -276,14 +278,16 @@ __global__ void __launch_bounds__(256) raster_kernel(FrameConst fc, RasterArgs a
     }
 }
 
-void launch_raster(const FrameConst &fc, const RasterArgs &a, bool f16, int sms, cudaStream_t s) {
+void launch_raster(const FrameConst &fc, const RasterArgs &a, int attr, int sms, cudaStream_t s) {
     (void)sms;
     if (a.n <= 0) return;
     const int64_t blocks = (a.n + kChunk - 1) / kChunk;
-    if (f16)
-        raster_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
+    if (attr == 1)
+        raster_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
+    else if (attr == 2)
+        raster_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
     else
-        raster_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
+        raster_kernel<0><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
 }
 
 // ---------------------------------------------------------------------------

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libsplotch.so")
 
 SPL_OK, SPL_EINVAL, SPL_ENOMEM, SPL_ECUDA, SPL_ESTATE, SPL_EDEVICE, SPL_ELIMIT = range(7)
 SPL_MEM_HOST, SPL_MEM_DEVICE = 0, 1
-SPL_ATTR_F32, SPL_ATTR_F16 = 0, 1
+SPL_ATTR_F32, SPL_ATTR_F16, SPL_ATTR_F16_IS = 0, 1, 2
 SPL_MODE_ADDITIVE, SPL_MODE_EA = 0, 1
 SPL_SCHED_NONE, SPL_SCHED_COUNT, SPL_SCHED_MLP = 0, 1, 2
 
@@ -182,12 +182,13 @@ class Renderer:
         return self._h
 
     def load(self, parts: dict, fp16: dict | None = None):
-        """Load particles; fp16 (optional) holds h, I, s as binary16 arrays."""
+        """Load particles.  fp16 (optional) holds binary16 arrays that replace
+        parts' h, I and s (SPL_ATTR_F16), or only I and s (SPL_ATTR_F16_IS)."""
         src = dict(parts)
         attr = SPL_ATTR_F32
         if fp16 is not None:
             src.update(fp16)
-            attr = SPL_ATTR_F16
+            attr = SPL_ATTR_F16 if "h" in fp16 else SPL_ATTR_F16_IS
         arrs = [src[k] for k in ("x", "y", "z", "h", "I", "s")]
         on_dev = [hasattr(a, "is_cuda") and a.is_cuda for a in arrs]
         if any(on_dev) and not all(on_dev):
@@ -195,7 +196,10 @@ class Renderer:
         n = int(arrs[0].shape[0])
         if not any(on_dev):
             arrs = [np.ascontiguousarray(a) for a in arrs]
-            for a, want in zip(arrs, [np.float32] * 3 + [np.float16 if attr else np.float32] * 3):
+            half_h = attr == SPL_ATTR_F16
+            wants = [np.float32] * 3 + [np.float16 if half_h else np.float32] + \
+                [np.float16 if attr != SPL_ATTR_F32 else np.float32] * 2
+            for a, want in zip(arrs, wants):
                 if a.dtype != want or a.shape != (n,):
                     raise ValueError("particle arrays: wrong dtype or shape")
         p = spl_particles(n, *[_ptr(a) for a in arrs], attr,
