@@ -158,11 +158,29 @@ int spl_render(spl_ctx *ctx, float *d_image, void *stream);
  * to h_image (width*height*3 floats); returns when the copy has completed. */
 int spl_render_host(spl_ctx *ctx, float *h_image);
 
-/* Render n_views cameras of the same particle set; d_images[k] (device) holds
- * cams[k].width * cams[k].height * 3 floats.  All views are binned first and
- * rendered by one persistent launch over every (view, tile) work item. */
+/* Render n_views (1 .. 64) cameras of the loaded particle set in one batch;
+ * d_images[k] (device) receives cams[k].width * cams[k].height * 3 floats.
+ * The particles are rasterised for every view by one launch (each particle
+ * is read from HBM once per batch, then hits in L2), the views' tile lists
+ * share one scan, and one persistent launch renders every (view, tile) work
+ * item, so that light and heavy views balance each other.  The first call
+ * for a configuration (number of views, image sizes, parameters, particle
+ * count) renders eagerly and then captures the whole pipeline into a CUDA
+ * graph; later calls with the same configuration -- the cameras themselves
+ * may move -- replay that graph.  A replay whose lists outgrow the captured
+ * capacities is detected on the device and the batch is rendered again
+ * eagerly.  Returns after the batch has finished. */
 int spl_render_batch(spl_ctx *ctx, const spl_camera *cams, int32_t n_views,
                      float *const *d_images, void *stream);
+
+/* Autotuner (the empirical tuning of tile size and chunking of Sec. 5.1,
+ * done by timing): renders the batch with every candidate tile side
+ * (16, 32, 64) and class-radius pair (r_small, r_large) in {(2, 32), (4, 64),
+ * (8, 128), (4, inf)}, reps timed renders each, keeps the fastest as the
+ * context's parameters and returns it in *best (and its time per batch in
+ * *best_ms; either may be NULL).  The images are overwritten. */
+int spl_autotune(spl_ctx *ctx, const spl_camera *cams, int32_t n_views, float *const *d_images,
+                 int32_t reps, spl_params *best, float *best_ms);
 
 int spl_get_stats(spl_ctx *ctx, spl_stats *out);
 int spl_set_timing(spl_ctx *ctx, int32_t enable);   /* per-stage CUDA events; resets sums */

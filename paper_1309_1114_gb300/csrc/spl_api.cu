@@ -70,13 +70,26 @@ struct spl_ctx {
     spl_params par{};
     // scratch
     DevBuf<float4> rec0, rec1;
-    DevBuf<int> counts, offsets, cursor;
+    DevBuf<int> counts;
+    DevBuf<long long> offsets, cursor;
     DevBuf<unsigned> large_ids, entries;
     DevBuf<int> item_counts, item_offsets;
     DevBuf<WorkItem> items;
     DevBuf<DevStats> dstats;
     DevBuf<float> host_img_scratch;
     DevStats *hstats = nullptr;   // pinned
+    // views of the current batch: constants and image pointers, staged in
+    // pinned memory and copied to the device by every render (also inside a
+    // captured graph, where the copies read the staging at replay time)
+    DevBuf<FrameConst> d_fcs;
+    DevBuf<float *> d_images;
+    FrameConst *h_fcs = nullptr;  // pinned, kMaxViews
+    float **h_images = nullptr;   // pinned, kMaxViews
+    // CUDA graph of the batch pipeline (spl_render_batch)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    unsigned long long graph_key = 0;   // configuration the graph was captured for
+    unsigned long long buf_gen = 0;     // bumped whenever a scratch buffer moves
     // timing: two event sets, so that a frame's stage times are read at the
     // next frame's synchronisation point without an extra wait
     bool timing = false;
@@ -176,6 +189,12 @@ extern "C" int spl_create(spl_ctx **out, int device, void *stream) {
     if (rc == SPL_OK && cudaMemset(c->dstats.p, 0, sizeof(DevStats)) != cudaSuccess) rc = SPL_ECUDA;
     if (rc == SPL_OK && cudaMallocHost((void **)&c->hstats, sizeof(DevStats)) != cudaSuccess)
         rc = SPL_ENOMEM;
+    if (rc == SPL_OK && cudaMallocHost((void **)&c->h_fcs, sizeof(FrameConst) * kMaxViews) != cudaSuccess)
+        rc = SPL_ENOMEM;
+    if (rc == SPL_OK && cudaMallocHost((void **)&c->h_images, sizeof(float *) * kMaxViews) != cudaSuccess)
+        rc = SPL_ENOMEM;
+    if (rc == SPL_OK && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = SPL_ECUDA;
     for (int k = 0; rc == SPL_OK && k < 12; ++k)
         if (cudaEventCreate(&c->ev[k / 6][k % 6]) != cudaSuccess) rc = SPL_ECUDA;
     if (rc != SPL_OK) {
@@ -200,7 +219,12 @@ extern "C" int spl_destroy(spl_ctx *c) {
     c->large_ids.release(); c->entries.release(); c->dstats.release();
     c->item_counts.release(); c->item_offsets.release(); c->items.release();
     c->host_img_scratch.release();
+    c->d_fcs.release(); c->d_images.release();
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->hstats) cudaFreeHost(c->hstats);
+    if (c->h_fcs) cudaFreeHost(c->h_fcs);
+    if (c->h_images) cudaFreeHost(c->h_images);
     for (auto &set : c->ev)
         for (auto &e : set)
             if (e) cudaEventDestroy(e);
@@ -383,25 +407,65 @@ static void record_event(spl_ctx *c, int k, cudaStream_t s) {
     if (c->timing) cudaEventRecord(c->ev[c->ev_set][k], s);
 }
 
-// One frame with camera cam into d_image (device) on stream s.
-static int render_frame(spl_ctx *c, const spl_camera &cam, float *d_image, cudaStream_t s) {
-    if (!c->have_particles || !c->have_cam || c->npal < 1) return SPL_ESTATE;
-    const FrameConst fc = make_frame(c, cam);
-    const size_t n = (size_t)c->n;
-    SPL_TRY(c->rec0.ensure(n ? n : 1));
-    SPL_TRY(c->rec1.ensure(n ? n : 1));
-    SPL_TRY(c->large_ids.ensure(n ? n : 1));
-    SPL_TRY(c->counts.ensure((size_t)NLIST * fc.ntiles));
-    SPL_TRY(c->offsets.ensure((size_t)NLIST * fc.ntiles + 1));
-    SPL_TRY(c->cursor.ensure((size_t)NLIST * fc.ntiles));
-    SPL_TRY(c->item_counts.ensure((size_t)2 * fc.ntiles));
-    SPL_TRY(c->item_offsets.ensure((size_t)2 * fc.ntiles + 1));
-    SPL_TRY(c->entries.ensure(16));
-    SPL_CUDA(cudaGetLastError());
+// ---------------------------------------------------------------------------
+// The pipeline over a batch of views (a single frame is a batch of one).
+// ---------------------------------------------------------------------------
 
-    record_event(c, 0, s);
-    SPL_CUDA(cudaMemsetAsync(c->counts.p, 0, sizeof(int) * NLIST * fc.ntiles, s));
-    SPL_CUDA(cudaMemsetAsync(c->dstats.p, 0, offsetof(DevStats, err), s));
+// Grow buffer b to n elements; note when it moved (a captured graph holds
+// its old address).
+template <typename T>
+static int grow(spl_ctx *c, DevBuf<T> &b, size_t n) {
+    if (n <= b.cap && b.p) return SPL_OK;
+    c->buf_gen++;
+    return b.ensure(n);
+}
+
+// Per-view constants into the pinned staging; sizes every per-batch buffer
+// that does not depend on the binning results.
+static int prepare_views(spl_ctx *c, const spl_camera *cams, int V, float *const *images,
+                         Views &vs) {
+    if (V < 1 || V > kMaxViews) return SPL_EINVAL;
+    int tiles = 0;
+    for (int v = 0; v < V; ++v) {
+        FrameConst fc = make_frame(c, cams[v]);
+        fc.view = v;
+        fc.tile_base = tiles;
+        fc.slot_base = NLIST * tiles;
+        fc.rec_base = (long long)v * c->n;
+        if ((int64_t)tiles + fc.ntiles > (int64_t)0x7FFFFFFF / (2 * NLIST)) return SPL_EINVAL;
+        tiles += fc.ntiles;
+        c->h_fcs[v] = fc;
+        c->h_images[v] = images[v];
+    }
+    if ((int64_t)V * c->n > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // record ids are 32-bit
+    const size_t recs = (size_t)V * (size_t)c->n;
+    SPL_TRY(grow(c, c->rec0, recs ? recs : 1));
+    SPL_TRY(grow(c, c->rec1, recs ? recs : 1));
+    SPL_TRY(grow(c, c->large_ids, recs ? recs : 1));
+    SPL_TRY(grow(c, c->counts, (size_t)NLIST * tiles));
+    SPL_TRY(grow(c, c->offsets, (size_t)NLIST * tiles + 1));
+    SPL_TRY(grow(c, c->cursor, (size_t)NLIST * tiles));
+    SPL_TRY(grow(c, c->item_counts, (size_t)2 * tiles));
+    SPL_TRY(grow(c, c->item_offsets, (size_t)2 * tiles + 1));
+    SPL_TRY(grow(c, c->entries, 16));
+    SPL_TRY(grow(c, c->items, 16));
+    SPL_TRY(grow(c, c->d_fcs, kMaxViews));
+    SPL_TRY(grow(c, c->d_images, kMaxViews));
+    vs.fcs = c->d_fcs.p;
+    vs.nviews = V;
+    vs.total_tiles = tiles;
+    vs.tile = c->par.tile_px;
+    vs.n = c->n;
+    return SPL_OK;
+}
+
+// Stage 1: constants to the device, rasterise every view, count and scan the
+// list slots and the work items.
+static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
+    cudaMemcpyAsync(c->d_fcs.p, c->h_fcs, sizeof(FrameConst) * vs.nviews, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->d_images.p, c->h_images, sizeof(float *) * vs.nviews, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(c->counts.p, 0, sizeof(int) * NLIST * vs.total_tiles, s);
+    cudaMemsetAsync(c->dstats.p, 0, offsetof(DevStats, err), s);
     RasterArgs ra{};
     ra.n = c->n;
     ra.x = c->x.p; ra.y = c->y.p; ra.z = c->z.p;
@@ -411,66 +475,54 @@ static int render_frame(spl_ctx *c, const spl_camera &cam, float *d_image, cudaS
     ra.counts = c->counts.p;
     ra.large_ids = c->large_ids.p;
     ra.st = c->dstats.p;
-    launch_raster(fc, ra, c->attr_type, c->sms, s);
+    launch_raster(vs, ra, c->attr_type, s);
     record_event(c, 1, s);
     BinArgs ba{};
-    ba.n = c->n;
     ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
     ba.large_ids = c->large_ids.p;
     ba.counts = c->counts.p;
     ba.cursor = c->cursor.p;
     ba.st = c->dstats.p;
-    launch_count_large(fc, ba, c->sms, s);
-    launch_scan(NLIST * fc.ntiles, c->counts.p, c->offsets.p, c->cursor.p, NLIST,
-                c->dstats.p->totals, s);
-    launch_item_counts(fc, c->offsets.p, c->item_counts.p, s);
-    launch_scan(2 * fc.ntiles, c->item_counts.p, c->item_offsets.p, nullptr, 2,
+    launch_count_large(vs, ba, c->sms, s);
+    launch_scan(NLIST * vs.total_tiles, c->counts.p, c->offsets.p, c->cursor.p, 1,
+                &c->dstats.p->slot_total, s);
+    launch_item_counts(vs, c->offsets.p, c->item_counts.p, c->dstats.p, s);
+    launch_scan(2 * vs.total_tiles, c->item_counts.p, c->item_offsets.p, nullptr, 2,
                 c->dstats.p->item_totals, s);
-    SPL_CUDA(cudaGetLastError());
-    SPL_CUDA(cudaMemcpyAsync(c->hstats, c->dstats.p, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
-    SPL_CUDA(cudaStreamSynchronize(s));
-    harvest_timing(c, c->ev_set ^ 1);   // the previous frame has finished
-    if (c->hstats->err) {
-        // a device-side check failed in this or an earlier frame
-        SPL_CUDA(cudaMemsetAsync(&c->dstats.p->err, 0, sizeof(unsigned), s));
-        return SPL_EDEVICE;
-    }
-    int64_t total = 0;
-    for (int k = 0; k < NLIST; ++k) total += c->hstats->totals[k];
-    if (total > (int64_t)0x7FFFFFFF) return SPL_ENOMEM;   // list positions are int32
-    const int n_tile_items = c->hstats->item_totals[0];
-    const int n_large_items = c->hstats->item_totals[1];
-    SPL_TRY(c->entries.ensure((size_t)(total ? total : 1)));
-    SPL_TRY(c->items.ensure((size_t)(n_tile_items + n_large_items + 1)));
-    SPL_CUDA(cudaMemsetAsync(d_image, 0, sizeof(float) * 3 * (size_t)cam.width * cam.height, s));
+}
+
+// Stage 2: clear the images, fill the tile lists and work items, render.
+static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStream_t s) {
+    launch_zero_images(vs, c->d_images.p, c->sms, s);
+    BinArgs ba{};
+    ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
+    ba.large_ids = c->large_ids.p;
+    ba.counts = c->counts.p;
+    ba.cursor = c->cursor.p;
     ba.entries = c->entries.p;
     ba.entries_cap = (int64_t)c->entries.cap;
-    launch_scatter(fc, ba, c->sms, s);
-    launch_fill_items(fc, c->offsets.p, c->item_offsets.p, c->items.p, s);
+    ba.st = c->dstats.p;
+    launch_scatter(vs, ba, c->sms, s);
+    launch_fill_items(vs, c->offsets.p, c->item_offsets.p, c->items.p, (int)c->items.cap,
+                      c->dstats.p, s);
     record_event(c, 2, s);
     TileArgs ta{};
     ta.rec0 = c->rec0.p; ta.rec1 = c->rec1.p;
     ta.offsets = c->offsets.p;
     ta.entries = c->entries.p;
     ta.items = c->items.p;
-    ta.image = d_image;
+    ta.items_cap = (int)c->items.cap;
+    ta.images = c->d_images.p;
     ta.st = c->dstats.p;
-    launch_tile_pass(fc, ta, n_tile_items, c->sms, s);
+    launch_tile_pass(vs, ta, c->sms, s);
     record_event(c, 3, s);
-    launch_large_pass(fc, ta, n_tile_items, n_large_items, c->sms, s);
+    if (large_pass) launch_large_pass(vs, ta, c->sms, s);
     record_event(c, 4, s);
-    if (c->par.mode == SPL_MODE_EA)
-        launch_epilogue_ea(d_image, (int64_t)3 * cam.width * cam.height, c->sms, s);
+    if (c->par.mode == SPL_MODE_EA) launch_epilogue_views(vs, c->d_images.p, c->sms, s);
     record_event(c, 5, s);
-    SPL_CUDA(cudaGetLastError());
+}
 
-    int launches = 4 + (c->n > 0 ? 4 : 0) + (n_tile_items > 0 ? 1 : 0);
-    if (n_large_items > 0) launches += 1;
-    if (c->par.mode == SPL_MODE_EA) launches += 1;
-    if (c->timing) {
-        c->ev_pending[c->ev_set] = true;
-        c->ev_set ^= 1;
-    }
+static void fill_stats(spl_ctx *c, const Views &vs, int launches) {
     spl_stats &st = c->last;
     std::memset(&st, 0, sizeof(st));
     st.launches = launches;
@@ -481,16 +533,52 @@ static int render_frame(spl_ctx *c, const spl_camera &cam, float *d_image, cudaS
     st.n_medium = (int64_t)c->hstats->n_medium;
     st.n_large = (int64_t)c->hstats->n_large;
     for (int k = 0; k < NLIST; ++k) st.n_entries[k] = c->hstats->totals[k];
-    st.n_tiles = fc.ntiles;
-    st.tile_px = fc.tile;
+    st.n_tiles = vs.total_tiles;
+    st.tile_px = vs.tile;
+}
+
+// Eager render of a batch: binning, one synchronisation to size the lists
+// exactly, then the passes.
+static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const *images,
+                        cudaStream_t s) {
+    if (!c->have_particles || c->npal < 1) return SPL_ESTATE;
+    Views vs{};
+    SPL_TRY(prepare_views(c, cams, V, images, vs));
+    SPL_CUDA(cudaGetLastError());
+    record_event(c, 0, s);
+    enqueue_binning(c, vs, s);
+    SPL_CUDA(cudaGetLastError());
+    SPL_CUDA(cudaMemcpyAsync(c->hstats, c->dstats.p, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    SPL_CUDA(cudaStreamSynchronize(s));
+    harvest_timing(c, c->ev_set ^ 1);   // the previous frame has finished
+    if (c->hstats->err) {
+        // a device-side check failed in this or an earlier frame
+        SPL_CUDA(cudaMemsetAsync(&c->dstats.p->err, 0, sizeof(unsigned), s));
+        return SPL_EDEVICE;
+    }
+    const int64_t total = c->hstats->slot_total;
+    const int n_tile_items = c->hstats->item_totals[0];
+    const int n_large_items = c->hstats->item_totals[1];
+    SPL_TRY(grow(c, c->entries, (size_t)(total ? total : 1)));
+    SPL_TRY(grow(c, c->items, (size_t)(n_tile_items + n_large_items + 1)));
+    enqueue_render(c, vs, n_large_items > 0, s);
+    SPL_CUDA(cudaGetLastError());
+    const int launches = 5 + (c->n > 0 ? 4 : 0) + 1 + (n_large_items > 0 ? 1 : 0) +
+                         (c->par.mode == SPL_MODE_EA ? 1 : 0);
+    if (c->timing) {
+        c->ev_pending[c->ev_set] = true;
+        c->ev_set ^= 1;
+    }
+    fill_stats(c, vs, launches);
     return SPL_OK;
 }
 
 extern "C" int spl_render(spl_ctx *c, float *d_image, void *stream) {
     if (!c || !d_image) return SPL_EINVAL;
+    if (!c->have_cam) return SPL_ESTATE;
     DeviceGuard g(c->device);
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-    return render_frame(c, c->cam, d_image, s);
+    return render_views(c, &c->cam, 1, &d_image, s);
 }
 
 extern "C" int spl_render_host(spl_ctx *c, float *h_image) {
@@ -499,21 +587,170 @@ extern "C" int spl_render_host(spl_ctx *c, float *h_image) {
     DeviceGuard g(c->device);
     const size_t nv = (size_t)3 * c->cam.width * c->cam.height;
     SPL_TRY(c->host_img_scratch.ensure(nv));
-    SPL_TRY(render_frame(c, c->cam, c->host_img_scratch.p, c->stream));
+    float *img = c->host_img_scratch.p;
+    SPL_TRY(render_views(c, &c->cam, 1, &img, c->stream));
     SPL_CUDA(cudaMemcpyAsync(h_image, c->host_img_scratch.p, nv * sizeof(float),
                              cudaMemcpyDeviceToHost, c->stream));
     SPL_CUDA(cudaStreamSynchronize(c->stream));
     return SPL_OK;
 }
 
+// Configuration a captured batch graph is valid for: everything that shapes
+// the launches or the buffer sizes (cameras themselves may change: their
+// constants are copied from the pinned staging at replay time).
+static unsigned long long batch_key(const spl_ctx *c, const spl_camera *cams, int V) {
+    unsigned long long h = 1469598103934665603ULL;
+    auto mix = [&h](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t k = 0; k < n; ++k) h = (h ^ b[k]) * 1099511628211ULL;
+    };
+    mix(&V, sizeof(V));
+    for (int v = 0; v < V; ++v) {
+        mix(&cams[v].width, sizeof(cams[v].width));
+        mix(&cams[v].height, sizeof(cams[v].height));
+    }
+    mix(&c->par, sizeof(c->par));
+    mix(&c->n, sizeof(c->n));
+    mix(&c->attr_type, sizeof(c->attr_type));
+    mix(&c->npal, sizeof(c->npal));
+    mix(&c->buf_gen, sizeof(c->buf_gen));
+    return h;
+}
+
+// Capture the whole batch pipeline (no host synchronisation inside) on the
+// private capture stream; list and item capacities are the current ones.
+static int capture_batch(spl_ctx *c, const Views &vs, unsigned long long key) {
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    const bool timing = c->timing;
+    c->timing = false;   // no events inside the graph
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        enqueue_binning(c, vs, c->cap_stream);
+        enqueue_render(c, vs, true, c->cap_stream);
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+    }
+    c->timing = timing;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->graph = nullptr;
+        return SPL_ECUDA;
+    }
+    c->graph_key = key;
+    return SPL_OK;
+}
+
 extern "C" int spl_render_batch(spl_ctx *c, const spl_camera *cams, int32_t n_views,
                                 float *const *d_images, void *stream) {
-    if (!c || !cams || !d_images || n_views < 0) return SPL_EINVAL;
+    if (!c || !cams || !d_images || n_views < 0 || n_views > kMaxViews) return SPL_EINVAL;
     for (int v = 0; v < n_views; ++v)
         if (!camera_ok(&cams[v]) || !d_images[v]) return SPL_EINVAL;
+    if (n_views == 0) return SPL_OK;
+    if (!c->have_particles || c->npal < 1) return SPL_ESTATE;
     DeviceGuard g(c->device);
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-    for (int v = 0; v < n_views; ++v) SPL_TRY(render_frame(c, cams[v], d_images[v], s));
+    const unsigned long long key = batch_key(c, cams, n_views);
+    if (c->graph && c->graph_key == key) {
+        // replay: stage the constants, launch, check the device-side guards
+        Views vs{};
+        SPL_TRY(prepare_views(c, cams, n_views, d_images, vs));
+        if (batch_key(c, cams, n_views) == key) {
+            record_event(c, 0, s);
+            SPL_CUDA(cudaGraphLaunch(c->graph, s));
+            record_event(c, 5, s);
+            SPL_CUDA(cudaMemcpyAsync(c->hstats, c->dstats.p, sizeof(DevStats),
+                                     cudaMemcpyDeviceToHost, s));
+            SPL_CUDA(cudaStreamSynchronize(s));
+            if (!c->hstats->err) {
+                if (c->timing) {
+                    // only the total is timed inside a graph
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, c->ev[c->ev_set][0], c->ev[c->ev_set][5]);
+                    for (int k = 0; k < 6; ++k) c->last_ms[k] = 0.f;
+                    c->last_ms[5] = ms;
+                    c->sum_ms[5] += ms;
+                    c->timed_frames += 1;
+                }
+                fill_stats(c, vs, 1);
+                return SPL_OK;
+            }
+            // a list outgrew its captured capacity: clear and render eagerly
+            SPL_CUDA(cudaMemsetAsync(&c->dstats.p->err, 0, sizeof(unsigned), s));
+            SPL_CUDA(cudaStreamSynchronize(s));
+        }
+    }
+    // eager render (exact list sizes), then capture a graph for the next call
+    SPL_TRY(render_views(c, cams, n_views, d_images, s));
+    SPL_CUDA(cudaStreamSynchronize(s));
+    harvest_timing(c, c->ev_set ^ 1);
+    Views vs{};
+    SPL_TRY(prepare_views(c, cams, n_views, d_images, vs));
+    // headroom so that small changes of the cameras still fit the graph
+    SPL_TRY(grow(c, c->entries, c->entries.cap + c->entries.cap / 4));
+    SPL_TRY(grow(c, c->items, c->items.cap + c->items.cap / 4));
+    SPL_TRY(capture_batch(c, vs, batch_key(c, cams, n_views)));
+    return SPL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: tile side and class radii for a batch (Sec. 5.1 tunes n_p and
+// t_x empirically for occupancy; here the candidates are timed directly).
+// ---------------------------------------------------------------------------
+extern "C" int spl_autotune(spl_ctx *c, const spl_camera *cams, int32_t n_views,
+                            float *const *d_images, int32_t reps, spl_params *best,
+                            float *best_ms) {
+    if (!c || !cams || !d_images || n_views < 1 || n_views > kMaxViews || reps < 1) return SPL_EINVAL;
+    for (int v = 0; v < n_views; ++v)
+        if (!camera_ok(&cams[v]) || !d_images[v]) return SPL_EINVAL;
+    if (!c->have_particles || c->npal < 1) return SPL_ESTATE;
+    DeviceGuard g(c->device);
+    static const int tiles[] = {16, 32, 64};
+    static const double radii[][2] = {{2.0, 32.0}, {4.0, 64.0}, {8.0, 128.0}, {4.0, 1e9}};
+    const spl_params base = c->par;
+    spl_params bp = base;
+    float bms = -1.f;
+    cudaStream_t s = c->stream;
+    const bool timing = c->timing;
+    c->timing = false;
+    cudaEvent_t e0 = c->ev[0][0], e1 = c->ev[0][5];
+    int rc = SPL_OK;
+    for (int t : tiles) {
+        for (const auto &rr : radii) {
+            spl_params q = base;
+            q.tile_px = t;
+            q.r_small = rr[0] > q.r_sml ? rr[0] : q.r_sml;
+            q.r_large = rr[1] > q.r_small ? rr[1] : q.r_small;
+            if (!params_ok(&q)) continue;
+            c->par = q;
+            rc = render_views(c, cams, n_views, d_images, s);   // warm-up, sizes the lists
+            if (rc != SPL_OK) break;
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < reps && rc == SPL_OK; ++k) rc = render_views(c, cams, n_views, d_images, s);
+            cudaEventRecord(e1, s);
+            if (rc != SPL_OK) break;
+            rc = cuda_status(cudaEventSynchronize(e1));
+            if (rc != SPL_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (bms < 0.f || ms < bms) {
+                bms = ms;
+                bp = q;
+            }
+        }
+        if (rc != SPL_OK) break;
+    }
+    c->timing = timing;
+    c->ev_pending[0] = c->ev_pending[1] = false;
+    c->par = rc == SPL_OK ? bp : base;
+    if (rc != SPL_OK) return rc;
+    if (best) *best = bp;
+    if (best_ms) *best_ms = bms;
     return SPL_OK;
 }
 
@@ -565,31 +802,20 @@ extern "C" int spl_count_work(spl_ctx *c, int64_t out[4]) {
     if (!c || !out) return SPL_EINVAL;
     if (!c->have_particles || !c->have_cam || c->npal < 1) return SPL_ESTATE;
     DeviceGuard g(c->device);
-    const FrameConst fc = make_frame(c, c->cam);
-    const size_t n = (size_t)c->n;
-    SPL_TRY(c->rec0.ensure(n ? n : 1));
-    SPL_TRY(c->rec1.ensure(n ? n : 1));
-    SPL_TRY(c->large_ids.ensure(n ? n : 1));
-    SPL_TRY(c->counts.ensure((size_t)NLIST * fc.ntiles));
+    Views vs{};
+    float *no_image = nullptr;
+    SPL_TRY(prepare_views(c, &c->cam, 1, &no_image, vs));
     DevBuf<unsigned long long> work;
     SPL_TRY(work.ensure(4));
     int rc = SPL_OK;
     cudaStream_t s = c->stream;
-    if (rc == SPL_OK) rc = cuda_status(cudaMemsetAsync(work.p, 0, 4 * sizeof(unsigned long long), s));
-    if (rc == SPL_OK) rc = cuda_status(cudaMemsetAsync(c->counts.p, 0, sizeof(int) * NLIST * fc.ntiles, s));
-    if (rc == SPL_OK) rc = cuda_status(cudaMemsetAsync(c->dstats.p, 0, offsetof(DevStats, err), s));
+    rc = cuda_status(cudaMemsetAsync(work.p, 0, 4 * sizeof(unsigned long long), s));
     if (rc == SPL_OK) {
-        RasterArgs ra{};
-        ra.n = c->n;
-        ra.x = c->x.p; ra.y = c->y.p; ra.z = c->z.p;
-        ra.h = c->h.p; ra.I = c->I.p; ra.s = c->s.p;
-        ra.pal = c->pal.p;
-        ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
-        ra.counts = c->counts.p;
-        ra.large_ids = c->large_ids.p;
-        ra.st = c->dstats.p;
-        launch_raster(fc, ra, c->attr_type, c->sms, s);
-        launch_count_work(fc, c->rec0.p, c->rec1.p, c->n, work.p, c->sms, s);
+        const bool timing = c->timing;
+        c->timing = false;
+        enqueue_binning(c, vs, s);
+        c->timing = timing;
+        launch_count_work(c->h_fcs[0], c->rec0.p, c->rec1.p, c->n, work.p, c->sms, s);
         unsigned long long h[4] = {0, 0, 0, 0};
         rc = cuda_status(cudaGetLastError());
         if (rc == SPL_OK) rc = cuda_status(cudaMemcpyAsync(h, work.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -624,12 +850,14 @@ constexpr size_t kNaRec1 = kNaRec0 + na_round(sizeof(float4) * kNaMaxParticles);
 constexpr size_t kNaLarge = kNaRec1 + na_round(sizeof(float4) * kNaMaxParticles);
 constexpr size_t kNaCounts = kNaLarge + na_round(sizeof(unsigned) * kNaMaxParticles);
 constexpr size_t kNaOffsets = kNaCounts + na_round(sizeof(int) * NLIST * kNaMaxTiles);
-constexpr size_t kNaCursor = kNaOffsets + na_round(sizeof(int) * (NLIST * kNaMaxTiles + 1));
-constexpr size_t kNaItemCounts = kNaCursor + na_round(sizeof(int) * NLIST * kNaMaxTiles);
+constexpr size_t kNaCursor = kNaOffsets + na_round(sizeof(long long) * (NLIST * kNaMaxTiles + 1));
+constexpr size_t kNaItemCounts = kNaCursor + na_round(sizeof(long long) * NLIST * kNaMaxTiles);
 constexpr size_t kNaItemOffsets = kNaItemCounts + na_round(sizeof(int) * 2 * kNaMaxTiles);
 constexpr size_t kNaEntries = kNaItemOffsets + na_round(sizeof(int) * (2 * kNaMaxTiles + 1));
 constexpr size_t kNaItems = kNaEntries + na_round(sizeof(unsigned) * kNaMaxEntries);
-constexpr size_t kNaBytes = kNaItems + na_round(sizeof(WorkItem) * kNaMaxItems);
+constexpr size_t kNaView = kNaItems + na_round(sizeof(WorkItem) * kNaMaxItems);
+constexpr size_t kNaImage = kNaView + na_round(sizeof(FrameConst));
+constexpr size_t kNaBytes = kNaImage + na_round(sizeof(float *));
 }  // namespace
 
 // The scratch itself (about 15 MiB).  In host code this name is only a
@@ -697,18 +925,33 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     float4 *rec1 = reinterpret_cast<float4 *>(base + kNaRec1);
     unsigned *large_ids = reinterpret_cast<unsigned *>(base + kNaLarge);
     int *counts = reinterpret_cast<int *>(base + kNaCounts);
-    int *offsets = reinterpret_cast<int *>(base + kNaOffsets);
-    int *cursor = reinterpret_cast<int *>(base + kNaCursor);
+    long long *offsets = reinterpret_cast<long long *>(base + kNaOffsets);
+    long long *cursor = reinterpret_cast<long long *>(base + kNaCursor);
     int *item_counts = reinterpret_cast<int *>(base + kNaItemCounts);
     int *item_offsets = reinterpret_cast<int *>(base + kNaItemOffsets);
     unsigned *entries = reinterpret_cast<unsigned *>(base + kNaEntries);
     WorkItem *items = reinterpret_cast<WorkItem *>(base + kNaItems);
+    FrameConst *d_fc = reinterpret_cast<FrameConst *>(base + kNaView);
+    float **d_img = reinterpret_cast<float **>(base + kNaImage);
     cudaStream_t s = (cudaStream_t)stream;
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    FrameConst fcv = fc;
+    fcv.view = 0;
+    fcv.tile_base = 0;
+    fcv.slot_base = 0;
+    fcv.rec_base = 0;
+    Views vs{};
+    vs.fcs = d_fc;
+    vs.nviews = 1;
+    vs.total_tiles = fc.ntiles;
+    vs.tile = fc.tile;
+    vs.n = p->n;
 
     // the array keeps the previous call's contents: clear what starts at zero
     SPL_CUDA(cudaMemcpyAsync(pal, rgb, sizeof(float) * 3 * npal, cudaMemcpyHostToDevice, s));
+    SPL_CUDA(cudaMemcpyAsync(d_fc, &fcv, sizeof(FrameConst), cudaMemcpyHostToDevice, s));
+    SPL_CUDA(cudaMemcpyAsync(d_img, &d_image, sizeof(float *), cudaMemcpyHostToDevice, s));
     SPL_CUDA(cudaMemsetAsync(dst, 0, sizeof(DevStats), s));
     SPL_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * NLIST * fc.ntiles, s));
     RasterArgs ra{};
@@ -720,44 +963,42 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     ra.counts = counts;
     ra.large_ids = large_ids;
     ra.st = dst;
-    launch_raster(fc, ra, p->attr_type, sms, s);
+    launch_raster(vs, ra, p->attr_type, s);
     BinArgs ba{};
-    ba.n = p->n;
     ba.rec0 = rec0; ba.rec1 = rec1;
     ba.large_ids = large_ids;
     ba.counts = counts;
     ba.cursor = cursor;
     ba.st = dst;
-    launch_count_large(fc, ba, sms, s);
-    launch_scan(NLIST * fc.ntiles, counts, offsets, cursor, NLIST, dst->totals, s);
-    launch_item_counts(fc, offsets, item_counts, s);
+    launch_count_large(vs, ba, sms, s);
+    launch_scan(NLIST * fc.ntiles, counts, offsets, cursor, 1, &dst->slot_total, s);
+    launch_item_counts(vs, offsets, item_counts, dst, s);
     launch_scan(2 * fc.ntiles, item_counts, item_offsets, nullptr, 2, dst->item_totals, s);
     SPL_CUDA(cudaGetLastError());
     DevStats h;
     SPL_CUDA(cudaMemcpyAsync(&h, dst, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
     SPL_CUDA(cudaStreamSynchronize(s));
     if (h.err) return SPL_EDEVICE;
-    int64_t total = 0;
-    for (int k = 0; k < NLIST; ++k) total += h.totals[k];
+    const int64_t total = h.slot_total;
     const int n_tile_items = h.item_totals[0], n_large_items = h.item_totals[1];
     if (total > kNaMaxEntries || (int64_t)n_tile_items + n_large_items > kNaMaxItems)
         return SPL_ELIMIT;
-    SPL_CUDA(cudaMemsetAsync(d_image, 0, sizeof(float) * 3 * (size_t)cam->width * cam->height, s));
+    launch_zero_images(vs, d_img, sms, s);
     ba.entries = entries;
     ba.entries_cap = kNaMaxEntries;
-    launch_scatter(fc, ba, sms, s);
-    launch_fill_items(fc, offsets, item_offsets, items, s);
+    launch_scatter(vs, ba, sms, s);
+    launch_fill_items(vs, offsets, item_offsets, items, kNaMaxItems, dst, s);
     TileArgs ta{};
     ta.rec0 = rec0; ta.rec1 = rec1;
     ta.offsets = offsets;
     ta.entries = entries;
     ta.items = items;
-    ta.image = d_image;
+    ta.items_cap = kNaMaxItems;
+    ta.images = d_img;
     ta.st = dst;
-    launch_tile_pass(fc, ta, n_tile_items, sms, s);
-    launch_large_pass(fc, ta, n_tile_items, n_large_items, sms, s);
-    if (tmp.par.mode == SPL_MODE_EA)
-        launch_epilogue_ea(d_image, (int64_t)3 * cam->width * cam->height, sms, s);
+    launch_tile_pass(vs, ta, sms, s);
+    if (n_large_items > 0) launch_large_pass(vs, ta, sms, s);
+    if (tmp.par.mode == SPL_MODE_EA) launch_epilogue_views(vs, d_img, sms, s);
     SPL_CUDA(cudaGetLastError());
     return SPL_OK;
 }

@@ -46,6 +46,23 @@ struct FrameConst {
     int npal;
     int width, height;
     int tile, ntx, nty, ntiles;
+    // place of this view in a batch of views
+    int view;                  // index in the batch
+    int tile_base;             // first global tile: global tile = tile_base + local tile
+    int slot_base;             // first list slot: slot = slot_base + list * ntiles + tile
+    int pad_;
+    long long rec_base;        // first record: record = rec_base + particle id
+};
+
+// A batch of views rendered together: one particle set, nviews cameras.
+// Per-view constants live in device memory; the tile side is common.
+constexpr int kMaxViews = 64;
+struct Views {
+    const FrameConst *fcs;     // device, nviews entries
+    int nviews;
+    int total_tiles;           // sum over views of ntiles
+    int tile;                  // common tile side
+    int64_t n;                 // particles
 };
 
 // Device status block (one per context).
@@ -53,19 +70,28 @@ struct FrameConst {
 // accumulates until the host reads and clears it.
 struct DevStats {
     unsigned long long n_active, n_point, n_small, n_medium, n_large;
-    unsigned int n_large_ids;  // large particles appended this frame
-    int totals[NLIST];         // entries per list (written by the first scan)
+    unsigned int n_large_ids;  // large records appended this frame
+    int totals[NLIST];         // entries per list, summed over views
+    long long slot_total;      // all entries (written by the slot scan)
     int item_totals[2];        // work items of the tile pass and of the large pass
     int item_counter[2];       // dynamic work-item counters of the two passes
     unsigned int err;          // ERR_* bits
 };
 
-// A work item of the persistent tile / large passes: a tile and a range of
-// one of its lists, or (list == -1) every list of a tile light enough to be
-// done by one CTA, which then stores its pixels instead of adding them.
+// A work item of the persistent tile / large passes: a tile (global index
+// over the batch) and a range of one of its lists, or every list of a tile
+// light enough to be done by one CTA, which then stores its pixels instead of
+// adding them.  lv packs the view (high bits) and the list (low 8 bits, 0xFF
+// for "every list").
 struct WorkItem {
-    int tile, list, start, end;
+    int tile, lv;
+    long long start, end;
 };
+constexpr int kAllLists = 0xFF;
+__host__ __device__ inline int item_view(const WorkItem &w) { return w.lv >> 8; }
+__host__ __device__ inline int item_list(const WorkItem &w) {
+    return (w.lv & 0xFF) == kAllLists ? -1 : (w.lv & 0xFF);
+}
 
 // Largest list segment one work item takes (per list), so that a crowded
 // tile (a halo core holding 1e5-1e6 particles) is spread over many CTAs.
@@ -76,49 +102,67 @@ struct RasterArgs {
     const float *x, *y, *z;
     const void *h, *I, *s;
     const float *pal;          // npal * 3
-    float4 *rec0, *rec1;
-    int *counts;               // [NLIST][ntiles]
-    unsigned *large_ids;       // capacity n
+    float4 *rec0, *rec1;       // nviews * n records
+    int *counts;               // list slots of all views
+    unsigned *large_ids;       // record indices, capacity nviews * n
     DevStats *st;
 };
 
 struct BinArgs {
-    int64_t n;
     const float4 *rec0, *rec1;
     const unsigned *large_ids;
-    int *cursor;               // [NLIST][ntiles], starts as the offsets
+    long long *cursor;         // list slots, starts as the offsets
     int *counts;
-    unsigned *entries;
+    unsigned *entries;         // record indices
     int64_t entries_cap;
     DevStats *st;
 };
 
 struct TileArgs {
     const float4 *rec0, *rec1;
-    const int *offsets;        // [NLIST * ntiles + 1]
+    const long long *offsets;  // list slots of all views, + 1 (64-bit list positions)
     const unsigned *entries;
     const WorkItem *items;
-    float *image;
+    int items_cap;
+    float *const *images;      // device array: one image per view
     DevStats *st;
 };
 
-// Launchers (stream-ordered, no synchronisation).
-void launch_raster(const FrameConst &fc, const RasterArgs &a, int attr, int sms, cudaStream_t s);
-void launch_count_large(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s);
+// Launchers (stream-ordered, no synchronisation).  Every count the kernels
+// need after binning (entries, work items) is read from device memory, so
+// the whole sequence can be captured in a CUDA graph.
+void launch_raster(const Views &v, const RasterArgs &a, int attr, cudaStream_t s);
+void launch_count_large(const Views &v, const BinArgs &a, int sms, cudaStream_t s);
 // Exclusive scan of in[0..m) into out[0..m] (out[m] = total); cursor (may be
 // null) receives a copy of out[0..m); seg_totals[k] = total of the k-th of
 // nseg equal segments.
+void launch_scan(int m, const int *in, long long *out, long long *cursor, int nseg,
+                 long long *seg_totals, cudaStream_t s);
 void launch_scan(int m, const int *in, int *out, int *cursor, int nseg, int *seg_totals,
                  cudaStream_t s);
-void launch_item_counts(const FrameConst &fc, const int *offsets, int *item_counts, cudaStream_t s);
-void launch_fill_items(const FrameConst &fc, const int *offsets, const int *item_offsets,
-                       WorkItem *items, cudaStream_t s);
-void launch_scatter(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s);
-void launch_tile_pass(const FrameConst &fc, const TileArgs &a, int n_items, int sms, cudaStream_t s);
-void launch_large_pass(const FrameConst &fc, const TileArgs &a, int item0, int n_items, int sms,
-                       cudaStream_t s);
+void launch_item_counts(const Views &v, const long long *offsets, int *item_counts, DevStats *st,
+                        cudaStream_t s);
+void launch_fill_items(const Views &v, const long long *offsets, const int *item_offsets,
+                       WorkItem *items, int items_cap, DevStats *st, cudaStream_t s);
+void launch_scatter(const Views &v, const BinArgs &a, int sms, cudaStream_t s);
+void launch_tile_pass(const Views &v, const TileArgs &a, int sms, cudaStream_t s);
+void launch_large_pass(const Views &v, const TileArgs &a, int sms, cudaStream_t s);
 void launch_epilogue_ea(float *image, int64_t nvals, int sms, cudaStream_t s);
+// Zero every view's image / apply the E=A map to every view's image (the
+// image pointers are read from device memory, so a graph can replay them).
+void launch_zero_images(const Views &v, float *const *images, int sms, cudaStream_t s);
+void launch_epilogue_views(const Views &v, float *const *images, int sms, cudaStream_t s);
 void launch_count_work(const FrameConst &fc, const float4 *rec0, const float4 *rec1, int64_t n,
                        unsigned long long *work, int sms, cudaStream_t s);
+
+// View of a global tile index (binary search over the views' tile bases).
+__device__ __forceinline__ int view_of_tile(const FrameConst *fcs, int nviews, int g) {
+    int lo = 0, hi = nviews - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (fcs[mid].tile_base <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 }  // namespace spl

@@ -210,51 +210,85 @@ __device__ __forceinline__ void hash_clear(int *keys, int *vals) {
     }
 }
 
+// Flush the CTA's hash table into the global slot counts and clear it.
+__device__ __forceinline__ void hash_flush(int *keys, int *vals, int *gcounts) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
+        if (keys[k] >= 0) atomicAdd(&gcounts[keys[k]], vals[k]);
+        keys[k] = -1;
+        vals[k] = 0;
+    }
+    __syncthreads();
+}
+
+// Load view v's constants into shared memory (the whole CTA waits).
+__device__ __forceinline__ void load_view(const FrameConst *fcs, int v, FrameConst *sfc) {
+    __syncthreads();
+    const int words = (int)(sizeof(FrameConst) / sizeof(int));
+    for (int k = threadIdx.x; k < words; k += blockDim.x)
+        reinterpret_cast<int *>(sfc)[k] = reinterpret_cast<const int *>(fcs + v)[k];
+    __syncthreads();
+}
+
+// One thread per particle and view: the particle's chunk is rasterised for
+// every view of the batch (its inputs are read from HBM once and then hit in
+// L2), records are written to rec[view * n + id], list entries are counted.
 // ATTR: 0 = h, I, s in FP32; 1 = all three in binary16; 2 = h in FP32, I and s
 // in binary16.
 template <int ATTR>
-__global__ void __launch_bounds__(256) raster_kernel(FrameConst fc, RasterArgs a) {
+__global__ void __launch_bounds__(256) raster_kernel(Views vs, RasterArgs a) {
     __shared__ float spal[3 * kMaxPalette];
     __shared__ int keys[kHash], vals[kHash];
     __shared__ unsigned long long bstat[5];
-    for (int k = threadIdx.x; k < 3 * fc.npal; k += blockDim.x) spal[k] = a.pal[k];
+    __shared__ FrameConst sfc;
     hash_clear(keys, vals);
     if (threadIdx.x < 5) bstat[threadIdx.x] = 0;
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     unsigned n_act = 0, n_pt = 0, n_sm = 0, n_md = 0, n_lg = 0;
     const int64_t c0 = (int64_t)blockIdx.x * kChunk;
     const int64_t c1 = c0 + kChunk < a.n ? c0 + kChunk : a.n;
-    // all lanes of a warp run the same number of iterations (warp collectives)
-    for (int64_t base = c0; base < c1; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const bool valid = i < c1;
-        int cls = CLS_INACTIVE;
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
-        if (valid) {
-            cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_attr<ATTR == 1>(a.h, i),
-                             load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i), r0, r1);
-            a.rec0[i] = r0;
-            a.rec1[i] = r1;
+    for (int v = 0; v < vs.nviews; ++v) {
+        load_view(vs.fcs, v, &sfc);
+        const FrameConst &fc = sfc;
+        for (int k = threadIdx.x; k < 3 * fc.npal; k += blockDim.x) spal[k] = a.pal[k];
+        __syncthreads();
+        // all lanes of a warp run the same number of iterations (warp collectives)
+        for (int64_t base = c0; base < c1; base += blockDim.x) {
+            const int64_t i = base + threadIdx.x;
+            const bool valid = i < c1;
+            int cls = CLS_INACTIVE;
+            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
+            const int64_t rec = fc.rec_base + i;
+            if (valid) {
+                cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_attr<ATTR == 1>(a.h, i),
+                                 load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i), r0, r1);
+                a.rec0[rec] = r0;
+                a.rec1[rec] = r1;
+            }
+            const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0};
+            const int maxk = __reduce_max_sync(0xffffffffu, foot.nbox);
+            for (int k = 0; k < maxk; ++k) {
+                const int ls = foot_slot(fc, foot, k, r0, r1);
+                count_round(ls >= 0 ? fc.slot_base + ls : -1, keys, vals, a.counts, lane);
+            }
+            n_act += cls != CLS_INACTIVE;
+            n_pt += cls == CLS_POINT;
+            n_sm += cls == CLS_SMALL;
+            n_md += cls == CLS_MEDIUM;
+            n_lg += cls == CLS_LARGE;
+            // append large records to the large list (one atomic per warp)
+            const unsigned big = __ballot_sync(0xffffffffu, cls == CLS_LARGE);
+            if (big) {
+                unsigned basek = 0;
+                const int leader = __ffs(big) - 1;
+                if (lane == leader) basek = atomicAdd(&a.st->n_large_ids, (unsigned)__popc(big));
+                basek = __shfl_sync(0xffffffffu, basek, leader);
+                if (cls == CLS_LARGE)
+                    a.large_ids[basek + __popc(big & ((1u << lane) - 1u))] = (unsigned)rec;
+            }
         }
-        const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0};
-        const int maxk = __reduce_max_sync(0xffffffffu, foot.nbox);
-        for (int k = 0; k < maxk; ++k) count_round(foot_slot(fc, foot, k, r0, r1), keys, vals, a.counts, lane);
-        n_act += cls != CLS_INACTIVE;
-        n_pt += cls == CLS_POINT;
-        n_sm += cls == CLS_SMALL;
-        n_md += cls == CLS_MEDIUM;
-        n_lg += cls == CLS_LARGE;
-        // append large particles to the large list (one atomic per warp)
-        const unsigned big = __ballot_sync(0xffffffffu, cls == CLS_LARGE);
-        if (big) {
-            unsigned basek = 0;
-            const int leader = __ffs(big) - 1;
-            if (lane == leader) basek = atomicAdd(&a.st->n_large_ids, (unsigned)__popc(big));
-            basek = __shfl_sync(0xffffffffu, basek, leader);
-            if (cls == CLS_LARGE)
-                a.large_ids[basek + __popc(big & ((1u << lane) - 1u))] = (unsigned)i;
-        }
+        // one global atomic per distinct slot of this CTA and view
+        hash_flush(keys, vals, a.counts);
     }
     n_act = __reduce_add_sync(0xffffffffu, n_act);
     n_pt = __reduce_add_sync(0xffffffffu, n_pt);
@@ -269,40 +303,38 @@ __global__ void __launch_bounds__(256) raster_kernel(FrameConst fc, RasterArgs a
         atomicAdd(&bstat[4], (unsigned long long)n_lg);
     }
     __syncthreads();
-    // flush: one global atomic per distinct slot of this CTA
-    for (int k = threadIdx.x; k < kHash; k += blockDim.x)
-        if (keys[k] >= 0) atomicAdd(&a.counts[keys[k]], vals[k]);
     if (threadIdx.x < 5 && bstat[threadIdx.x]) {
         // n_active .. n_large are consecutive fields of DevStats
         atomicAdd(&a.st->n_active + threadIdx.x, bstat[threadIdx.x]);
     }
 }
 
-void launch_raster(const FrameConst &fc, const RasterArgs &a, int attr, int sms, cudaStream_t s) {
-    (void)sms;
-    if (a.n <= 0) return;
+void launch_raster(const Views &vs, const RasterArgs &a, int attr, cudaStream_t s) {
+    if (a.n <= 0 || vs.nviews <= 0) return;
     const int64_t blocks = (a.n + kChunk - 1) / kChunk;
     if (attr == 1)
-        raster_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
+        raster_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
     else if (attr == 2)
-        raster_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
+        raster_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
     else
-        raster_kernel<0><<<(unsigned)blocks, 256, 0, s>>>(fc, a);
+        raster_kernel<0><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
 }
 
 // ---------------------------------------------------------------------------
-// Large particles: one warp per particle walks its (possibly thousands of)
-// tiles.  mode 0 counts entries, mode 1 scatters ids through the cursors.
+// Large particles: one warp per large record walks its (possibly thousands
+// of) tiles.  mode 0 counts entries, mode 1 scatters record indices through
+// the cursors.
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(256) large_tiles_kernel(FrameConst fc, BinArgs a) {
+__global__ void __launch_bounds__(256) large_tiles_kernel(Views vs, BinArgs a) {
     const int lane = threadIdx.x & 31;
     const unsigned nl = a.st->n_large_ids;
     const unsigned warps = gridDim.x * (blockDim.x >> 5);
     for (unsigned w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nl; w += warps) {
-        const unsigned id = a.large_ids[w];
-        const float4 r0 = a.rec0[id];
-        const float4 r1 = a.rec1[id];
+        const unsigned rec = a.large_ids[w];
+        const FrameConst &fc = vs.fcs[(int)(rec / (unsigned long long)vs.n)];
+        const float4 r0 = a.rec0[rec];
+        const float4 r1 = a.rec1[rec];
         PixBox b;
         if (!splat_box(fc, r0, r1.x, b)) continue;
         const int tx0 = b.i0 / fc.tile, ty0 = b.j0 / fc.tile;
@@ -311,13 +343,14 @@ __global__ void __launch_bounds__(256) large_tiles_kernel(FrameConst fc, BinArgs
         for (int k = lane; k < nt; k += 32) {
             const int tx = tx0 + k % ntx, ty = ty0 + k / ntx;
             if (!disc_meets_tile(fc, r0, r1.x, tx, ty)) continue;
-            const int slot = L_LARGE * fc.ntiles + ty * fc.ntx + tx;
+            const int slot = fc.slot_base + L_LARGE * fc.ntiles + ty * fc.ntx + tx;
             if (MODE == 0) {
                 atomicAdd(&a.counts[slot], 1);
             } else {
-                const int pos = atomicAdd(&a.cursor[slot], 1);
+                const long long pos =
+                    (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.cursor[slot]), 1ULL);
                 if (pos < a.entries_cap)
-                    a.entries[pos] = id;
+                    a.entries[pos] = rec;
                 else
                     atomicOr(&a.st->err, ERR_LIST_OVERFLOW);
             }
@@ -325,46 +358,47 @@ __global__ void __launch_bounds__(256) large_tiles_kernel(FrameConst fc, BinArgs
     }
 }
 
-void launch_count_large(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s) {
-    if (a.n <= 0) return;
-    large_tiles_kernel<0><<<sms * 2, 256, 0, s>>>(fc, a);
+void launch_count_large(const Views &vs, const BinArgs &a, int sms, cudaStream_t s) {
+    if (vs.n <= 0) return;
+    large_tiles_kernel<0><<<sms * 2, 256, 0, s>>>(vs, a);
 }
 
 // ---------------------------------------------------------------------------
 // Exclusive scan: one CTA of 1024 threads, each owning a contiguous run.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) scan_kernel(int m, const int *in, int *out, int *cursor,
-                                                    int nseg, int *seg_totals) {
-    __shared__ int wsum[32];
+template <typename OT>
+__global__ void __launch_bounds__(1024) scan_kernel(int m, const int *in, OT *out, OT *cursor,
+                                                    int nseg, OT *seg_totals) {
+    __shared__ OT wsum[32];
     const int t = threadIdx.x, per = (m + 1023) / 1024;
     const int lo = min(t * per, m), hi = min(lo + per, m);
-    int sum = 0;
-    for (int k = lo; k < hi; ++k) sum += in[k];
+    OT sum = 0;
+    for (int k = lo; k < hi; ++k) sum += (OT)in[k];
     const int lane = t & 31, warp = t >> 5;
-    int incl = sum;
+    OT incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        OT v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
     }
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int v = wsum[lane];
-        int w = v;
+        OT v = wsum[lane];
+        OT w = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, w, o);
+            OT u = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += u;
         }
         wsum[lane] = w - v;
     }
     __syncthreads();
-    int run = wsum[warp] + incl - sum;
+    OT run = wsum[warp] + incl - sum;
     for (int k = lo; k < hi; ++k) {
         out[k] = run;
         if (cursor) cursor[k] = run;
-        run += in[k];
+        run += (OT)in[k];
     }
     if (t == 1023) out[m] = run;
     __syncthreads();   // makes every thread's results visible to the block
@@ -374,9 +408,14 @@ __global__ void __launch_bounds__(1024) scan_kernel(int m, const int *in, int *o
     }
 }
 
+void launch_scan(int m, const int *in, long long *out, long long *cursor, int nseg,
+                 long long *seg_totals, cudaStream_t s) {
+    scan_kernel<long long><<<1, 1024, 0, s>>>(m, in, out, cursor, nseg, seg_totals);
+}
+
 void launch_scan(int m, const int *in, int *out, int *cursor, int nseg, int *seg_totals,
                  cudaStream_t s) {
-    scan_kernel<<<1, 1024, 0, s>>>(m, in, out, cursor, nseg, seg_totals);
+    scan_kernel<int><<<1, 1024, 0, s>>>(m, in, out, cursor, nseg, seg_totals);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,13 +426,20 @@ void launch_scan(int m, const int *in, int *out, int *cursor, int nseg, int *seg
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int div_up(int a, int b) { return (a + b - 1) / b; }
 
-__global__ void item_count_kernel(FrameConst fc, const int *off, int *item_counts) {
-    const int nt = fc.ntiles;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        const int cp = off[L_POINT * nt + t + 1] - off[L_POINT * nt + t];
-        const int cs = off[L_SMALL * nt + t + 1] - off[L_SMALL * nt + t];
-        const int cm = off[L_MEDIUM * nt + t + 1] - off[L_MEDIUM * nt + t];
-        const int cl = off[L_LARGE * nt + t + 1] - off[L_LARGE * nt + t];
+__global__ void item_count_kernel(Views vs, const long long *off, int *item_counts, DevStats *st) {
+    __shared__ int lt[NLIST];
+    if (threadIdx.x < NLIST) lt[threadIdx.x] = 0;
+    __syncthreads();
+    const int T = vs.total_tiles;
+    int tot[NLIST] = {0, 0, 0, 0};
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < T; g += gridDim.x * blockDim.x) {
+        const FrameConst &fc = vs.fcs[view_of_tile(vs.fcs, vs.nviews, g)];
+        const int t = g - fc.tile_base, nt = fc.ntiles, sb = fc.slot_base;
+        const int cp = (int)(off[sb + L_POINT * nt + t + 1] - off[sb + L_POINT * nt + t]);
+        const int cs = (int)(off[sb + L_SMALL * nt + t + 1] - off[sb + L_SMALL * nt + t]);
+        const int cm = (int)(off[sb + L_MEDIUM * nt + t + 1] - off[sb + L_MEDIUM * nt + t]);
+        const int cl = (int)(off[sb + L_LARGE * nt + t + 1] - off[sb + L_LARGE * nt + t]);
+        tot[0] += cp; tot[1] += cs; tot[2] += cm; tot[3] += cl;
         int n = 0;
         if (cp + cs + cm > 0) {
             if (cp <= kSegPoint && cs <= kSegSmall && cm <= kSegMedium)
@@ -401,38 +447,61 @@ __global__ void item_count_kernel(FrameConst fc, const int *off, int *item_count
             else
                 n = div_up(cp, kSegPoint) + div_up(cs, kSegSmall) + div_up(cm, kSegMedium);
         }
-        item_counts[t] = n;
-        item_counts[nt + t] = div_up(cl, kSegLarge);
+        item_counts[g] = n;
+        item_counts[T + g] = div_up(cl, kSegLarge);
     }
+    for (int l = 0; l < NLIST; ++l) {
+        const int v = __reduce_add_sync(0xffffffffu, tot[l]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&lt[l], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < NLIST && lt[threadIdx.x]) atomicAdd(&st->totals[threadIdx.x], lt[threadIdx.x]);
 }
 
-void launch_item_counts(const FrameConst &fc, const int *offsets, int *item_counts, cudaStream_t s) {
-    item_count_kernel<<<(fc.ntiles + 255) / 256, 256, 0, s>>>(fc, offsets, item_counts);
+void launch_item_counts(const Views &vs, const long long *offsets, int *item_counts, DevStats *st,
+                        cudaStream_t s) {
+    const int blocks = (vs.total_tiles + 255) / 256;
+    item_count_kernel<<<blocks, 256, 0, s>>>(vs, offsets, item_counts, st);
 }
 
-__global__ void fill_items_kernel(FrameConst fc, const int *off, const int *ioff, WorkItem *items) {
-    const int nt = fc.ntiles;
+__device__ __forceinline__ void put_item(WorkItem *items, int cap, int pos, WorkItem w, DevStats *st) {
+    if (pos < cap)
+        items[pos] = w;
+    else
+        atomicOr(&st->err, ERR_LIST_OVERFLOW);
+}
+
+__global__ void fill_items_kernel(Views vs, const long long *off, const int *ioff, WorkItem *items,
+                                  int cap, DevStats *st) {
+    const int T = vs.total_tiles;
     const int seg[NLIST] = {kSegPoint, kSegSmall, kSegMedium, kSegLarge};
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        int w = ioff[t];
-        const int nw = ioff[t + 1] - w;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < T; g += gridDim.x * blockDim.x) {
+        const int v = view_of_tile(vs.fcs, vs.nviews, g);
+        const FrameConst &fc = vs.fcs[v];
+        const int t = g - fc.tile_base, nt = fc.ntiles, sb = fc.slot_base;
+        int w = ioff[g];
+        const int nw = ioff[g + 1] - w;
         if (nw == 1) {
-            items[w] = {t, -1, 0, 0};
+            put_item(items, cap, w, {g, (v << 8) | kAllLists, 0, 0}, st);
         } else if (nw > 1) {
             for (int l = 0; l < L_LARGE; ++l) {
-                const int b = off[l * nt + t], e = off[l * nt + t + 1];
-                for (int k = b; k < e; k += seg[l]) items[w++] = {t, l, k, min(k + seg[l], e)};
+                const long long b = off[sb + l * nt + t], e = off[sb + l * nt + t + 1];
+                for (long long k = b; k < e; k += seg[l])
+                    put_item(items, cap, w++, {g, (v << 8) | l, k, k + seg[l] < e ? k + seg[l] : e}, st);
             }
         }
-        int wl = ioff[nt + t];
-        const int b = off[L_LARGE * nt + t], e = off[L_LARGE * nt + t + 1];
-        for (int k = b; k < e; k += kSegLarge) items[wl++] = {t, L_LARGE, k, min(k + kSegLarge, e)};
+        int wl = ioff[T + g];
+        const long long b = off[sb + L_LARGE * nt + t], e = off[sb + L_LARGE * nt + t + 1];
+        for (long long k = b; k < e; k += kSegLarge)
+            put_item(items, cap, wl++,
+                     {g, (v << 8) | L_LARGE, k, k + kSegLarge < e ? k + kSegLarge : e}, st);
     }
 }
 
-void launch_fill_items(const FrameConst &fc, const int *offsets, const int *item_offsets,
-                       WorkItem *items, cudaStream_t s) {
-    fill_items_kernel<<<(fc.ntiles + 255) / 256, 256, 0, s>>>(fc, offsets, item_offsets, items);
+void launch_fill_items(const Views &vs, const long long *offsets, const int *item_offsets,
+                       WorkItem *items, int items_cap, DevStats *st, cudaStream_t s) {
+    const int blocks = (vs.total_tiles + 255) / 256;
+    fill_items_kernel<<<blocks, 256, 0, s>>>(vs, offsets, item_offsets, items, items_cap, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -440,87 +509,104 @@ void launch_fill_items(const FrameConst &fc, const int *offsets, const int *item
 // tiles' lists (order inside a tile follows the atomics, which is harmless:
 // E_p = A_p makes the sum order-independent, Sec. 2).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ TileFoot load_foot(const FrameConst &fc, const BinArgs &a, int64_t i,
-                                              int64_t c1, float4 &r0, float4 &r1) {
+__device__ __forceinline__ TileFoot load_foot(const FrameConst &fc, const BinArgs &a, int64_t rec,
+                                              bool valid, float4 &r0, float4 &r1) {
     r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
-    if (i >= c1) return TileFoot{-1, 0, 0, 1, 0};
-    r1 = a.rec1[i];
+    if (!valid) return TileFoot{-1, 0, 0, 1, 0};
+    r1 = a.rec1[rec];
     const int cls = record_class(fc, r1.x);
     if (cls == CLS_INACTIVE || cls == CLS_LARGE) return TileFoot{-1, 0, 0, 1, 0};
-    r0 = a.rec0[i];
+    r0 = a.rec0[rec];
     return tile_footprint(fc, cls, r0, r1);
 }
 
-// Scatter particle ids of points, small and medium particles into their
-// tiles' lists.  Per CTA: count its chunk's slots in the shared hash table,
-// reserve one contiguous range per slot with one global atomic, then place
-// every entry at range base + local rank.  Order inside a tile follows the
-// atomics, which is harmless: E_p = A_p makes the sum order-independent
+// Scatter record indices of points, small and medium particles into their
+// tiles' lists.  Per CTA and view: count its chunk's slots in the shared hash
+// table, reserve one contiguous range per slot with one global atomic, then
+// place every entry at range base + local rank.  Order inside a tile follows
+// the atomics, which is harmless: E_p = A_p makes the sum order-independent
 // (Sec. 2).
-__global__ void __launch_bounds__(256) scatter_kernel(FrameConst fc, BinArgs a) {
-    __shared__ int keys[kHash], vals[kHash], bases[kHash];
-    hash_clear(keys, vals);
-    __syncthreads();
+__global__ void __launch_bounds__(256) scatter_kernel(Views vs, BinArgs a) {
+    extern __shared__ long long scatter_smem[];
+    long long *bases = scatter_smem;                         // kHash
+    int *keys = reinterpret_cast<int *>(bases + kHash);      // kHash
+    int *vals = keys + kHash;                                // kHash
+    __shared__ FrameConst sfc;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t c0 = (int64_t)blockIdx.x * kChunk;
-    const int64_t c1 = c0 + kChunk < a.n ? c0 + kChunk : a.n;
-    // pass 1: local counts
-    for (int64_t base = c0; base < c1; base += blockDim.x) {
-        float4 r0, r1;
-        const TileFoot f = load_foot(fc, a, base + threadIdx.x, c1, r0, r1);
-        const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
-        for (int k = 0; k < maxk; ++k) {
-            const int key = foot_slot(fc, f, k, r0, r1);
-            const unsigned m = __match_any_sync(0xffffffffu, key);
-            if (key >= 0 && lane == __ffs(m) - 1) {
-                const int slot = hash_slot(keys, key, true);
-                if (slot >= 0) atomicAdd(&vals[slot], __popc(m));
+    const int64_t c1 = c0 + kChunk < vs.n ? c0 + kChunk : vs.n;
+    for (int v = 0; v < vs.nviews; ++v) {
+        hash_clear(keys, vals);
+        load_view(vs.fcs, v, &sfc);
+        const FrameConst &fc = sfc;
+        // pass 1: local counts
+        for (int64_t base = c0; base < c1; base += blockDim.x) {
+            const int64_t i = base + threadIdx.x;
+            float4 r0, r1;
+            const TileFoot f = load_foot(fc, a, fc.rec_base + i, i < c1, r0, r1);
+            const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
+            for (int k = 0; k < maxk; ++k) {
+                const int ls = foot_slot(fc, f, k, r0, r1);
+                const int key = ls >= 0 ? fc.slot_base + ls : -1;
+                const unsigned m = __match_any_sync(0xffffffffu, key);
+                if (key >= 0 && lane == __ffs(m) - 1) {
+                    const int slot = hash_slot(keys, key, true);
+                    if (slot >= 0) atomicAdd(&vals[slot], __popc(m));
+                }
             }
         }
-    }
-    __syncthreads();
-    // reserve one range per slot
-    for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
-        if (keys[k] >= 0) bases[k] = atomicAdd(&a.cursor[keys[k]], vals[k]);
-        vals[k] = 0;
-    }
-    __syncthreads();
-    // pass 2: place the entries
-    for (int64_t base = c0; base < c1; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        float4 r0, r1;
-        const TileFoot f = load_foot(fc, a, i, c1, r0, r1);
-        const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
-        for (int k = 0; k < maxk; ++k) {
-            const int key = foot_slot(fc, f, k, r0, r1);
-            const unsigned m = __match_any_sync(0xffffffffu, key);
-            const int leader = __ffs(m) - 1;
-            int pos = 0;
-            if (key >= 0 && lane == leader) {
-                const int slot = hash_slot(keys, key, false);
-                if (slot >= 0)
-                    pos = bases[slot] + atomicAdd(&vals[slot], __popc(m));
-                else
-                    pos = atomicAdd(&a.cursor[key], __popc(m));
-            }
-            pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(m & lt);
-            if (key >= 0) {
-                if (pos < a.entries_cap)
-                    a.entries[pos] = (unsigned)i;
-                else
-                    atomicOr(&a.st->err, ERR_LIST_OVERFLOW);
+        __syncthreads();
+        // reserve one range per slot
+        for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
+            if (keys[k] >= 0)
+                bases[k] = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.cursor[keys[k]]),
+                                                (unsigned long long)vals[k]);
+            vals[k] = 0;
+        }
+        __syncthreads();
+        // pass 2: place the entries
+        for (int64_t base = c0; base < c1; base += blockDim.x) {
+            const int64_t i = base + threadIdx.x;
+            const int64_t rec = fc.rec_base + i;
+            float4 r0, r1;
+            const TileFoot f = load_foot(fc, a, rec, i < c1, r0, r1);
+            const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
+            for (int k = 0; k < maxk; ++k) {
+                const int ls = foot_slot(fc, f, k, r0, r1);
+                const int key = ls >= 0 ? fc.slot_base + ls : -1;
+                const unsigned m = __match_any_sync(0xffffffffu, key);
+                const int leader = __ffs(m) - 1;
+                long long pos = 0;
+                if (key >= 0 && lane == leader) {
+                    const int slot = hash_slot(keys, key, false);
+                    if (slot >= 0)
+                        pos = bases[slot] + atomicAdd(&vals[slot], __popc(m));
+                    else
+                        pos = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.cursor[key]),
+                                                   (unsigned long long)__popc(m));
+                }
+                pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(m & lt);
+                if (key >= 0) {
+                    if (pos < a.entries_cap)
+                        a.entries[pos] = (unsigned)rec;
+                    else
+                        atomicOr(&a.st->err, ERR_LIST_OVERFLOW);
+                }
             }
         }
+        __syncthreads();
     }
 }
 
-void launch_scatter(const FrameConst &fc, const BinArgs &a, int sms, cudaStream_t s) {
-    if (a.n <= 0) return;
-    const int64_t blocks = (a.n + kChunk - 1) / kChunk;
-    scatter_kernel<<<(unsigned)blocks, 256, 0, s>>>(fc, a);
-    large_tiles_kernel<1><<<sms * 2, 256, 0, s>>>(fc, a);
+void launch_scatter(const Views &vs, const BinArgs &a, int sms, cudaStream_t s) {
+    if (vs.n <= 0 || vs.nviews <= 0) return;
+    const int64_t blocks = (vs.n + kChunk - 1) / kChunk;
+    const size_t smem = (size_t)kHash * (sizeof(long long) + 2 * sizeof(int));
+    cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    scatter_kernel<<<(unsigned)blocks, 256, smem, s>>>(vs, a);
+    large_tiles_kernel<1><<<sms * 2, 256, 0, s>>>(vs, a);
 }
 
 // ---------------------------------------------------------------------------

@@ -203,10 +203,11 @@ constexpr size_t smem_bytes() {
 template <int T>
 constexpr int min_ctas() { return T >= 64 ? 2 : (T == 32 ? 5 : 4); }
 
-// Persistent pass over work items [item0, item0 + n_items).
+// Persistent pass over the work items of every view of the batch: the tile
+// pass takes items [0, item_totals[0]), the large pass the next
+// item_totals[1] (both counts read from device memory).
 template <int T, bool LARGE>
-__global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(FrameConst fc, TileArgs a,
-                                                                           int item0, int n_items) {
+__global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views vs, TileArgs a) {
     using S = Shape<T>;
     constexpr int NW = kTileThreads / 32;
     extern __shared__ float4 smem_raw[];
@@ -217,9 +218,11 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Frame
     float (*sacc)[T][T] = reinterpret_cast<float (*)[T][T]>(&swx[S::P][0]);
     __shared__ unsigned band_mask[NW], full_mask[NW];
     __shared__ int s_item;
+    __shared__ FrameConst sfc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nt = fc.ntiles;
     int *counter = &a.st->item_counter[LARGE ? 1 : 0];
+    const int item0 = LARGE ? a.st->item_totals[0] : 0;
+    const int n_items = min(a.st->item_totals[LARGE ? 1 : 0], a.items_cap - item0);
     for (;;) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -228,16 +231,25 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Frame
         const int it = s_item;
         if (it >= n_items) break;
         const WorkItem w = a.items[item0 + it];
-        const int tile = w.tile;
+        const int view = item_view(w), list = item_list(w);
+        {
+            const int words = (int)(sizeof(FrameConst) / sizeof(int));
+            if (tid < words)
+                reinterpret_cast<int *>(&sfc)[tid] = reinterpret_cast<const int *>(vs.fcs + view)[tid];
+        }
+        __syncthreads();
+        const FrameConst &fc = sfc;
+        const int tile = w.tile - fc.tile_base;
         const int x0 = (tile % fc.ntx) * T, y0 = (tile / fc.ntx) * T;
-        int lb0 = 0, le0 = 0, lb1 = 0, le1 = 0, lb2 = 0, le2 = 0;
-        if (w.list < 0) {
-            lb0 = a.offsets[L_POINT * nt + tile]; le0 = a.offsets[L_POINT * nt + tile + 1];
-            lb1 = a.offsets[L_SMALL * nt + tile]; le1 = a.offsets[L_SMALL * nt + tile + 1];
-            lb2 = a.offsets[L_MEDIUM * nt + tile]; le2 = a.offsets[L_MEDIUM * nt + tile + 1];
-        } else if (w.list == L_POINT) {
+        const int nt = fc.ntiles, sb = fc.slot_base;
+        long long lb0 = 0, le0 = 0, lb1 = 0, le1 = 0, lb2 = 0, le2 = 0;
+        if (list < 0) {
+            lb0 = a.offsets[sb + L_POINT * nt + tile]; le0 = a.offsets[sb + L_POINT * nt + tile + 1];
+            lb1 = a.offsets[sb + L_SMALL * nt + tile]; le1 = a.offsets[sb + L_SMALL * nt + tile + 1];
+            lb2 = a.offsets[sb + L_MEDIUM * nt + tile]; le2 = a.offsets[sb + L_MEDIUM * nt + tile + 1];
+        } else if (list == L_POINT) {
             lb0 = w.start; le0 = w.end;
-        } else if (w.list == L_SMALL) {
+        } else if (list == L_SMALL) {
             lb1 = w.start; le1 = w.end;
         } else {
             lb2 = w.start; le2 = w.end;      // medium (tile pass) or large (large pass)
@@ -251,8 +263,8 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Frame
 
         // points (Sec. 4.1): batches of 256 staged records, warp-aggregated
 #pragma unroll 1
-        for (int base = lb0; base < le0; base += kTileThreads) {
-            const int cnt = min(kTileThreads, le0 - base);
+        for (long long base = lb0; base < le0; base += kTileThreads) {
+            const int cnt = (int)(le0 - base < kTileThreads ? le0 - base : kTileThreads);
             if (tid < cnt) {
                 const unsigned id = a.entries[base + tid];
                 st0[tid] = a.rec0[id];
@@ -264,8 +276,8 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Frame
         }
         // small particles: one warp each over the pixel box
 #pragma unroll 1
-        for (int base = lb1; base < le1; base += kTileThreads) {
-            const int cnt = min(kTileThreads, le1 - base);
+        for (long long base = lb1; base < le1; base += kTileThreads) {
+            const int cnt = (int)(le1 - base < kTileThreads ? le1 - base : kTileThreads);
             if (tid < cnt) {
                 const unsigned id = a.entries[base + tid];
                 st0[tid] = a.rec0[id];
@@ -285,8 +297,8 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Frame
             n1 = a.rec1[id];
         }
 #pragma unroll 1
-        for (int base = lb2; base < le2; base += S::P) {
-            const int cnt = min(S::P, le2 - base);
+        for (long long base = lb2; base < le2; base += S::P) {
+            const int cnt = (int)(le2 - base < S::P ? le2 - base : S::P);
             if (tid < cnt) {
                 st0[tid] = n0;
                 st1[tid] = n1;
@@ -315,7 +327,8 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Frame
         }
 
         // write: shared part + registers, stored (only item of its tile) or added
-        const bool store = !LARGE && w.list < 0;
+        const bool store = !LARGE && list < 0;
+        float *image = a.images[view];
 #pragma unroll
         for (int q = 0; q < S::RPL; ++q) {
             const int row = row0 + q;
@@ -323,7 +336,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Frame
             for (int k = 0; k < S::CPL; ++k) {
                 const int cx = col + 32 * k;
                 if (y0 + row >= fc.height || x0 + cx >= fc.width) continue;
-                float *dst = a.image + 3 * ((int64_t)(y0 + row) * fc.width + x0 + cx);
+                float *dst = image + 3 * ((int64_t)(y0 + row) * fc.width + x0 + cx);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const float v = sacc[c][row][cx] + acc[q][k][c];
@@ -338,35 +351,29 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Frame
 }
 
 template <int T, bool LARGE>
-static void launch_items_t(const FrameConst &fc, const TileArgs &a, int item0, int n_items, int sms,
-                           cudaStream_t s) {
+static void launch_items_t(const Views &vs, const TileArgs &a, int sms, cudaStream_t s) {
     constexpr size_t bytes = smem_bytes<T>();
     cudaFuncSetAttribute(item_kernel<T, LARGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)bytes);
-    const int cap = sms * min_ctas<T>();
-    const int g = n_items < cap ? n_items : cap;
-    item_kernel<T, LARGE><<<g, kTileThreads, bytes, s>>>(fc, a, item0, n_items);
+    item_kernel<T, LARGE><<<sms * min_ctas<T>(), kTileThreads, bytes, s>>>(vs, a);
 }
 
 template <bool LARGE>
-static void launch_items(const FrameConst &fc, const TileArgs &a, int item0, int n_items, int sms,
-                         cudaStream_t s) {
-    if (n_items <= 0) return;
-    if (fc.tile == 16)
-        launch_items_t<16, LARGE>(fc, a, item0, n_items, sms, s);
-    else if (fc.tile == 64)
-        launch_items_t<64, LARGE>(fc, a, item0, n_items, sms, s);
+static void launch_items(const Views &vs, const TileArgs &a, int sms, cudaStream_t s) {
+    if (vs.tile == 16)
+        launch_items_t<16, LARGE>(vs, a, sms, s);
+    else if (vs.tile == 64)
+        launch_items_t<64, LARGE>(vs, a, sms, s);
     else
-        launch_items_t<32, LARGE>(fc, a, item0, n_items, sms, s);
+        launch_items_t<32, LARGE>(vs, a, sms, s);
 }
 
-void launch_tile_pass(const FrameConst &fc, const TileArgs &a, int n_items, int sms, cudaStream_t s) {
-    launch_items<false>(fc, a, 0, n_items, sms, s);
+void launch_tile_pass(const Views &vs, const TileArgs &a, int sms, cudaStream_t s) {
+    launch_items<false>(vs, a, sms, s);
 }
 
-void launch_large_pass(const FrameConst &fc, const TileArgs &a, int item0, int n_items, int sms,
-                       cudaStream_t s) {
-    launch_items<true>(fc, a, item0, n_items, sms, s);
+void launch_large_pass(const Views &vs, const TileArgs &a, int sms, cudaStream_t s) {
+    launch_items<true>(vs, a, sms, s);
 }
 
 // E_p = A_p solution of Eq. 1 applied to the additive sum: I = 1 - exp(-S).
@@ -381,6 +388,26 @@ void launch_epilogue_ea(float *image, int64_t nvals, int sms, cudaStream_t s) {
     int64_t blocks = (nvals + 255) / 256;
     blocks = blocks < (int64_t)sms * 4 ? blocks : (int64_t)sms * 4;
     epilogue_ea_kernel<<<(unsigned)blocks, 256, 0, s>>>(image, nvals);
+}
+
+// Grid-stride over every pixel value of every view (blockIdx.y = view).
+template <bool EA>
+__global__ void views_pointwise_kernel(Views vs, float *const *images) {
+    const int v = blockIdx.y;
+    const FrameConst &fc = vs.fcs[v];
+    float *img = images[v];
+    const int64_t n = (int64_t)3 * fc.width * fc.height;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        img[i] = EA ? -expm1f(-img[i]) : 0.f;
+}
+
+void launch_zero_images(const Views &vs, float *const *images, int sms, cudaStream_t s) {
+    views_pointwise_kernel<false><<<dim3(sms * 2, vs.nviews), 256, 0, s>>>(vs, images);
+}
+
+void launch_epilogue_views(const Views &vs, float *const *images, int sms, cudaStream_t s) {
+    views_pointwise_kernel<true><<<dim3(sms * 2, vs.nviews), 256, 0, s>>>(vs, images);
 }
 
 }  // namespace spl

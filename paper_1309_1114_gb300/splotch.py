@@ -74,6 +74,8 @@ _SIGS = {
     "spl_set_timing": [_P, C.c_int32],
     "spl_get_records": [_P, C.c_int64, _P, _P, _P, _P, _P],
     "spl_count_work": [_P, C.POINTER(C.c_int64)],
+    "spl_autotune": [_P, C.POINTER(spl_camera), C.c_int32, C.POINTER(C.c_void_p), C.c_int32,
+                     C.POINTER(spl_params), C.POINTER(C.c_float)],
     "spl_render_noalloc": [C.POINTER(spl_particles), C.POINTER(spl_camera), C.POINTER(spl_params),
                            _P, C.c_int32, C.c_float, C.c_float, _P, C.c_int32, _P],
     "spl_error_string": [C.c_int],
@@ -242,6 +244,15 @@ class Renderer:
         check(load_library().spl_render_batch(self._h, arr, len(cams), ptrs, stream),
               "spl_render_batch")
         return images
+
+    def autotune(self, cams: list, images: list, reps: int = 2) -> tuple:
+        arr = (spl_camera * len(cams))(*[make_camera(c) for c in cams])
+        ptrs = (C.c_void_p * len(images))(*[im.data_ptr() for im in images])
+        best = spl_params()
+        ms = C.c_float(0.0)
+        check(load_library().spl_autotune(self._h, arr, len(cams), ptrs, int(reps), C.byref(best),
+                                          C.byref(ms)), "spl_autotune")
+        return {k: getattr(best, k) for k, _ in best._fields_}, float(ms.value)
 
     def stats(self) -> dict:
         s = spl_stats()
