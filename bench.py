@@ -45,6 +45,12 @@ WORKLOADS = {
                     "desc": "100M clustered particles, FP32 attributes, 2048x2048 RGB FP32"},
     "uniform": {"scene": "uniform", "label": "uniform-200k-256sq-f32",
                 "desc": "200k uniform particles, log-normal h, 256x256 RGB FP32"},
+    "pareto": {"scene": "pareto", "label": "pareto-400M-4096sq-f32", "sched": True,
+               "desc": "400M clustered particles, heavy-tailed smoothing lengths (Pareto alpha 1.5), "
+                       "4096x4096 RGB FP32, work items ordered by the tile-cost network"},
+    "orbit": {"scene": "orbit", "label": "orbit-20M-64views-512-2048", "batch": True,
+              "desc": "20M clustered particles, 64 views on an azimuth orbit (5.625 deg steps), "
+                      "resolutions cycling 512^2/1024^2/2048^2, one batched graph-replayed render"},
 }
 METRIC = "particles/s per GB300 at stated error vs FP64 oracle; % of HBM roofline"
 FLOPS_PER_PAIR = 7      # separable weight product (1 mul) + 3 multiply-adds
@@ -211,6 +217,161 @@ def run_reference(args, wl):
     return 0
 
 
+def run_batch(args, wl):
+    """Batched multi-view workload: a step renders every view of the orbit."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1309_1114_gb300.splotch import Renderer
+
+    scene = make_scene(wl)
+    cams = scene.cams
+    V = len(cams)
+    stream = torch.cuda.current_stream()
+    r = Renderer(local, stream.cuda_stream)
+    r.load(scene.parts)
+    r.set_colormap(scene.palette)
+    r.set_params()
+    imgs = [torch.empty((c["height"], c["width"], 3), device="cuda") for c in cams]
+    tuned, tuned_ms = r.autotune(cams, imgs, reps=1)      # picks tile and class radii
+    work = [0, 0, 0, 0]
+    for c in cams:
+        r.set_camera(c)
+        work = [a + b for a, b in zip(work, r.count_work())]
+    for _ in range(args.warmup):
+        r.render_batch(cams, imgs)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r.render_batch(cams, imgs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * V * scene.n / (ms * 1e-3)
+
+    # stage times of the same batch rendered eagerly (graph replay times only the total)
+    r.set_graph(False)
+    r.set_timing(True)
+    nst = max(2, min(args.steps, 5))
+    for _ in range(nst):
+        r.render_batch(cams, imgs)
+    st = r.stats()
+    r.set_timing(False)
+    r.set_graph(True)
+    nfr = max(st["timed_frames"], 1)
+    stage = dict(zip(["raster", "bin", "tile", "large", "epilogue", "total"],
+                     [v / nfr for v in st["sum_ms"]]))
+
+    # the plain form: one spl_render per view with default parameters
+    r.set_params()
+    for c, im in zip(cams[:3], imgs[:3]):
+        r.set_camera(c)
+        r.render(im)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for c, im in zip(cams, imgs):
+        r.set_camera(c)
+        r.render(im)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    r.set_params(**{k: tuned[k] for k in ("tile_px", "r_small", "r_large")})
+
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    dom = "tile" if stage["tile"] >= stage["large"] else "large"
+    flops = (FLOPS_PER_POINT * work[0] + FLOPS_PER_PAIR * (work[1] + work[2]) if dom == "tile"
+             else FLOPS_PER_PAIR * work[3])
+    achieved = flops / (stage[dom] * 1e-3) / 1e12 if stage[dom] > 0 else 0.0
+    kname = f"item_kernel<{tuned['tile_px']}, {0 if dom == 'tile' else 1}>"
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
+                "kernel": kname, "kernel_ms": stage[dom],
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                              f"{sm_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+                "work": {"point_deposits": work[0], "small_pairs": work[1],
+                         "medium_pairs": work[2], "large_pairs": work[3],
+                         "flops_per_pair": FLOPS_PER_PAIR},
+                "stage_basis": "eager batch with per-stage CUDA events"}
+    pix = sum(c["width"] * c["height"] for c in cams)
+    alg_bytes = scene.n * 24 + 12 * pix
+    hbm = float(peaks.get("hbm_gbs", 6771.1))
+
+    # end to end: upload the particles, render the batch, download every image
+    host_parts = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+                  for k, v in scene.parts.items()}
+    host_imgs = [torch.empty(tuple(im.shape), dtype=torch.float32).pin_memory() for im in imgs]
+    e2e_steps = 3
+    if ws > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r.load(host_parts)
+        r.render_batch(cams, imgs)
+        for im, h in zip(imgs, host_imgs):
+            h.copy_(im, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": ws * V * scene.n / e2e_s, "unit": "particles/s",
+           "h2d_bytes_per_step": scene.n * 24, "d2h_bytes_per_step": 12 * pix,
+           "ms_per_step": 1e3 * e2e_s}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, m, cores, secs = oracle_sample_rate(scene, cams[1], 10.0)
+        cpu = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
+               "sample": f"{m} particles drawn at random from the workload, one 1024x1024 view of "
+                         f"the orbit, FP64, OpenMP over {cores} threads, {secs:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["label"], "description": wl["desc"],
+                       "n_particles": scene.n, "n_views": V, "units": "particle-views",
+                       "autotuned": {k: tuned[k] for k in ("tile_px", "r_small", "r_large")},
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (20M particles = 480 MB); no flush"},
+            "plain_form": {"ms_per_step": plain_ms, "value": V * scene.n / (plain_ms * 1e-3),
+                           "note": "one spl_render per view, default parameters"},
+            "roofline": roofline,
+            "hbm_roofline_frac": alg_bytes / (ms * 1e-3) / (hbm * 1e9),
+            "hbm_alg_bytes_per_step": alg_bytes,
+            "stage_ms": stage,
+            "e2e": e2e,
+            "gpu_launches": 11 * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    r.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_ours(args, wl):
     import torch
     ws, rank, local = dist_env()
@@ -234,6 +395,18 @@ def run_ours(args, wl):
     r.set_colormap(scene.palette)
     r.set_camera(cam)
     r.set_params()
+    sched_mode = 0
+    model_info = None
+    if wl.get("sched"):
+        from paper_1309_1114_gb300 import scheduler, train_scheduler
+        sched_mode = 1
+        if os.path.exists(train_scheduler.DEFAULT_OUT):
+            theta, heur = scheduler.load(train_scheduler.DEFAULT_OUT)
+            r.set_model(theta, heur)
+            sched_mode = 2
+            with open(train_scheduler.DEFAULT_OUT) as fh:
+                model_info = {k: v for k, v in json.load(fh).items() if k not in ("theta", "heur")}
+        r.set_params(sched=sched_mode)
     img = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
     work = r.count_work()
 
@@ -286,6 +459,22 @@ def run_ours(args, wl):
                 "work": {"point_deposits": work[0], "small_pairs": work[1],
                          "medium_pairs": work[2], "large_pairs": work[3],
                          "flops_per_pair": FLOPS_PER_PAIR}}
+    schedulers = None
+    if wl.get("sched"):
+        # the same frame with each scheduler (CUDA-event frame times, 5 frames each)
+        schedulers = {}
+        for name, mode in (("none", 0), ("count", 1), ("network", 2)):
+            if mode == 2 and sched_mode != 2:
+                continue
+            r.set_params(sched=mode)
+            r.render(img)
+            r.set_timing(True)
+            for _ in range(5):
+                r.render(img)
+            sst = r.stats()
+            r.set_timing(False)
+            schedulers[name] = sst["sum_ms"][5] / max(sst["timed_frames"], 1)
+        r.set_params(sched=sched_mode)
     bytes_per_particle = {None: 24, "all": 18, "is": 20}[wl.get("fp16")]
     alg_bytes = scene.n * bytes_per_particle + 12 * W * H
     hbm = float(peaks.get("hbm_gbs", 6771.1))
@@ -342,6 +531,9 @@ def run_ours(args, wl):
             "hbm_roofline_frac": hbm_frac,
             "hbm_alg_bytes_per_step": alg_bytes,
             "stage_ms": stage,
+            "scheduler": {"mode": ["none", "count", "network"][sched_mode],
+                          "frame_ms_by_scheduler": schedulers, "model": model_info}
+            if wl.get("sched") else None,
             "stats": {k: st[k] for k in ("n_active", "n_point", "n_small", "n_medium", "n_large")}
             | {"n_entries": st["n_entries"], "n_tiles": st["n_tiles"]},
             "e2e": e2e,
@@ -370,6 +562,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if wl.get("batch"):
+        return run_batch(args, wl)
     return run_ours(args, wl)
 
 

@@ -185,11 +185,68 @@ int spl_autotune(spl_ctx *ctx, const spl_camera *cams, int32_t n_views, float *c
 int spl_get_stats(spl_ctx *ctx, spl_stats *out);
 int spl_set_timing(spl_ctx *ctx, int32_t enable);   /* per-stage CUDA events; resets sums */
 
+/* enable (default) or disable the CUDA-graph replay of spl_render_batch; with
+ * graphs disabled every batch renders eagerly, with per-stage timing. */
+int spl_set_graph(spl_ctx *ctx, int32_t enable);
+
 /* Work of the current camera and particle set, counted exactly by a separate
  * diagnostic kernel (not part of a render): out[0] = point deposits that land
  * on the image, out[1..3] = covered (particle, pixel) pairs, d^2 <= r^2, of
  * the small, medium and large classes.  Used for roofline accounting. */
 int spl_count_work(spl_ctx *ctx, int64_t out[4]);
+
+/* ---- Load balance: learned tile-cost scheduler --------------------------
+ * The render's work items (a tile with its lists, or a bounded segment of a
+ * crowded tile's list -- Sec. 4 Remarks note how unevenly particles fall into
+ * tiles) are taken by persistent CTAs.  With params.sched = SPL_SCHED_COUNT
+ * or SPL_SCHED_MLP they are taken longest-first by a predicted cost:
+ *   SPL_SCHED_COUNT  heur[0] + heur[1] * log1p(entries of the item);
+ *   SPL_SCHED_MLP    the tile-cost network y = w2 . relu(W1 x + b1) + b2,
+ *                    32 -> 64 -> 1 in FP32, on the item's 32 features (per
+ *                    radius bin b = clamp(floor(log2(r / 0.5)), 0, 15): x[b] =
+ *                    log1p(particles in bin b), x[16 + b] = log1p(tile pixels
+ *                    inside their boxes / tile area)); without a model it
+ *                    falls back to SPL_SCHED_COUNT.
+ * Parameter vector (SPL_MLP_NPARAM floats): W1[64][32] row-major, b1[64],
+ * w2[64], b2.  The paper has no counterpart to the network. */
+#define SPL_MLP_NPARAM 2177
+
+/* Load a model (theta: host, SPL_MLP_NPARAM floats, or NULL to keep) and/or
+ * the count heuristic's two coefficients (heur: host, or NULL to keep;
+ * default {0, 1}). */
+int spl_set_model(spl_ctx *ctx, const float *theta, const float *heur);
+
+/* With recording on, every render also stores each work item's features and
+ * the SM clock cycles its CTA spent on it (clock64 difference). */
+int spl_set_recording(spl_ctx *ctx, int32_t enable);
+
+/* Copy the last render's samples (at most cap) into DEVICE buffers:
+ * d_feat[n][32] features and d_logc[n] = log(cycles).  *n receives the count.
+ * Waits for the context stream.  SPL_ESTATE when recording is off. */
+int spl_get_samples(spl_ctx *ctx, float *d_feat, float *d_logc, int64_t cap, int64_t *n);
+
+int spl_mlp_nparam(void);   /* SPL_MLP_NPARAM */
+
+/* Network kernels on DEVICE buffers (stream: cudaStream_t or NULL).
+ * forward:   d_y[b] = net(d_x[b]) for b < B (d_x row-major [B][32]).
+ * loss_grad: d_grad = gradient of L = (1/B) sum_b (net(x_b) - t_b)^2 with
+ *            respect to every parameter, d_loss (may be NULL) = L; allocates
+ *            and frees its own scratch and waits for the stream.
+ * adam:      one Adam step (Kingma & Ba, Algorithm 1) on np parameters,
+ *            step >= 1, moments d_m, d_v updated in place. */
+int spl_mlp_forward(const float *d_theta, const float *d_x, int64_t B, float *d_y, void *stream);
+int spl_mlp_loss_grad(const float *d_theta, const float *d_x, const float *d_t, int64_t B,
+                      float *d_grad, float *d_loss, void *stream);
+int spl_mlp_adam(float *d_theta, const float *d_grad, float *d_m, float *d_v, int64_t np,
+                 int64_t step, float lr, float beta1, float beta2, float eps, void *stream);
+
+/* Full-batch training on the GPU: `steps` Adam steps (beta 0.9 / 0.999,
+ * eps 1e-8, learning rate lr) of the mean-squared-error loss on DEVICE
+ * samples d_x[B][32], d_t[B], starting from and returning theta (HOST,
+ * SPL_MLP_NPARAM floats); losses (HOST, steps floats, may be NULL) receives
+ * the loss before each step.  Allocates its own scratch. */
+int spl_mlp_train(const float *d_x, const float *d_t, int64_t B, float *theta, int32_t steps,
+                  float lr, float *losses, void *stream);
 
 /* Diagnostics used by the tests.  spl_get_records copies the last render's
  * per-particle rasterisation results for particles [0, n) into host arrays

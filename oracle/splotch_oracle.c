@@ -548,8 +548,10 @@ int orc_adam_step(double *theta, const double *grad, double *m, double *v,
 /* which only notes that particles per tile vary and unbalance the work).  */
 /* For an image cut into T x T tiles (the tiling of Eq. 8), a particle      */
 /* belongs to tile t when its pixel-centre bounding box (the pixels with    */
-/* |i+1/2-x_s| <= r and |j+1/2-y_s| <= r, cut to the image) meets t; a      */
-/* point-rule particle belongs to the tile of its pixel.  Per tile:         */
+/* |i+1/2-x_s| <= r and |j+1/2-y_s| <= r, cut to the image) meets t and the */
+/* disc reaches the centre of a pixel of t (a tile whose pixel centres all  */
+/* lie beyond r receives nothing, Eq. 2); a point-rule particle belongs to  */
+/* the tile of its pixel.  Per tile:                                        */
 /*   f[b]      = log1p(number of member particles with radius bin b)        */
 /*   f[16 + b] = log1p(sum over those particles of the number of tile       */
 /*               pixels inside their box, divided by area_scale)            */
@@ -595,6 +597,12 @@ int orc_tile_features(long n, const float *x, const float *y, const float *z,
             for (long tx = (long)i0 / tile; tx <= (long)i1 / tile; ++tx) {
                 double a0 = fmax(i0, (double)(tx * tile)), a1 = fmin(i1, (double)(tx * tile + tile - 1));
                 double c0 = fmax(j0, (double)(ty * tile)), c1 = fmin(j1, (double)(ty * tile + tile - 1));
+                if (o.cls == ORC_SPLAT) {
+                    /* nearest pixel centre of the tile to the particle */
+                    double ex = fmin(fmax(o.xs, tx * tile + 0.5), fmin((double)(tx * tile + tile), (double)v.w) - 0.5);
+                    double ey = fmin(fmax(o.ys, ty * tile + 0.5), fmin((double)(ty * tile + tile), (double)v.h) - 0.5);
+                    if ((ex - o.xs) * (ex - o.xs) + (ey - o.ys) * (ey - o.ys) > o.r * o.r) continue;
+                }
                 long t = ty * ntx + tx;
                 cnt[t * 16 + b] += 1.0;
                 area[t * 16 + b] += (a1 - a0 + 1.0) * (c1 - c0 + 1.0);

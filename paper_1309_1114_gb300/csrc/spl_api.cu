@@ -90,6 +90,14 @@ struct spl_ctx {
     cudaGraphExec_t graph = nullptr;
     unsigned long long graph_key = 0;   // configuration the graph was captured for
     unsigned long long buf_gen = 0;     // bumped whenever a scratch buffer moves
+    bool use_graph = true;
+    // scheduling of the work items, and the per-item samples that train it
+    DevBuf<float> feat, cost, theta, heur;
+    DevBuf<int> item_n, order, order_hist;
+    DevBuf<long long> item_cycles;
+    bool have_model = false;
+    bool recording = false;
+    int last_items = 0;                 // work items of the last eager render
     // timing: two event sets, so that a frame's stage times are read at the
     // next frame's synchronisation point without an extra wait
     bool timing = false;
@@ -195,6 +203,13 @@ extern "C" int spl_create(spl_ctx **out, int device, void *stream) {
         rc = SPL_ENOMEM;
     if (rc == SPL_OK && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = SPL_ECUDA;
+    if (rc == SPL_OK) rc = c->heur.ensure(2);
+    if (rc == SPL_OK) rc = c->theta.ensure(kNParam);
+    if (rc == SPL_OK) rc = c->order_hist.ensure(512);
+    if (rc == SPL_OK) {
+        const float h0[2] = {0.f, 1.f};   // count heuristic: log1p(entries)
+        if (cudaMemcpy(c->heur.p, h0, sizeof(h0), cudaMemcpyHostToDevice) != cudaSuccess) rc = SPL_ECUDA;
+    }
     for (int k = 0; rc == SPL_OK && k < 12; ++k)
         if (cudaEventCreate(&c->ev[k / 6][k % 6]) != cudaSuccess) rc = SPL_ECUDA;
     if (rc != SPL_OK) {
@@ -220,6 +235,8 @@ extern "C" int spl_destroy(spl_ctx *c) {
     c->item_counts.release(); c->item_offsets.release(); c->items.release();
     c->host_img_scratch.release();
     c->d_fcs.release(); c->d_images.release();
+    c->feat.release(); c->cost.release(); c->theta.release(); c->heur.release();
+    c->item_n.release(); c->order.release(); c->order_hist.release(); c->item_cycles.release();
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->hstats) cudaFreeHost(c->hstats);
@@ -296,6 +313,12 @@ extern "C" int spl_set_params(spl_ctx *c, const spl_params *q) {
 extern "C" int spl_get_params(spl_ctx *c, spl_params *out) {
     if (!c || !out) return SPL_EINVAL;
     *out = c->par;
+    return SPL_OK;
+}
+
+extern "C" int spl_set_graph(spl_ctx *c, int32_t enable) {
+    if (!c) return SPL_EINVAL;
+    c->use_graph = enable != 0;
     return SPL_OK;
 }
 
@@ -459,6 +482,17 @@ static int prepare_views(spl_ctx *c, const spl_camera *cams, int V, float *const
     return SPL_OK;
 }
 
+// Per-item buffers follow the capacity of the item array.
+static int size_item_buffers(spl_ctx *c) {
+    const size_t n = c->items.cap;
+    SPL_TRY(grow(c, c->feat, n * kFeat));
+    SPL_TRY(grow(c, c->cost, n));
+    SPL_TRY(grow(c, c->item_n, n));
+    SPL_TRY(grow(c, c->order, n));
+    SPL_TRY(grow(c, c->item_cycles, n));
+    return SPL_OK;
+}
+
 // Stage 1: constants to the device, rasterise every view, count and scan the
 // list slots and the work items.
 static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
@@ -505,7 +539,6 @@ static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
     launch_scatter(vs, ba, c->sms, s);
     launch_fill_items(vs, c->offsets.p, c->item_offsets.p, c->items.p, (int)c->items.cap,
                       c->dstats.p, s);
-    record_event(c, 2, s);
     TileArgs ta{};
     ta.rec0 = c->rec0.p; ta.rec1 = c->rec1.p;
     ta.offsets = c->offsets.p;
@@ -514,6 +547,21 @@ static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
     ta.items_cap = (int)c->items.cap;
     ta.images = c->d_images.p;
     ta.st = c->dstats.p;
+    // scheduling: per-item features, predicted cost, longest first
+    const bool sched = c->par.sched != SPL_SCHED_NONE;
+    // exact features when recording training samples, else a 64-entry sample
+    if (sched || c->recording)
+        launch_item_features(vs, ta, (float)vs.tile * (float)vs.tile, c->recording ? 0 : 64,
+                             c->feat.p, c->item_n.p, c->sms, s);
+    if (sched) {
+        const float *theta = c->par.sched == SPL_SCHED_MLP && c->have_model ? c->theta.p : nullptr;
+        launch_item_cost(c->feat.p, c->item_n.p, theta, c->heur.p, ta.items_cap, c->dstats.p,
+                         c->cost.p, s);
+        launch_order_items(c->cost.p, ta.items_cap, c->dstats.p, c->order_hist.p, c->order.p, s);
+        ta.order = c->order.p;
+    }
+    if (c->recording) ta.item_cycles = c->item_cycles.p;
+    record_event(c, 2, s);
     launch_tile_pass(vs, ta, c->sms, s);
     record_event(c, 3, s);
     if (large_pass) launch_large_pass(vs, ta, c->sms, s);
@@ -561,10 +609,14 @@ static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const 
     const int n_large_items = c->hstats->item_totals[1];
     SPL_TRY(grow(c, c->entries, (size_t)(total ? total : 1)));
     SPL_TRY(grow(c, c->items, (size_t)(n_tile_items + n_large_items + 1)));
+    SPL_TRY(size_item_buffers(c));
+    c->last_items = n_tile_items + n_large_items;
     enqueue_render(c, vs, n_large_items > 0, s);
     SPL_CUDA(cudaGetLastError());
     const int launches = 5 + (c->n > 0 ? 4 : 0) + 1 + (n_large_items > 0 ? 1 : 0) +
-                         (c->par.mode == SPL_MODE_EA ? 1 : 0);
+                         (c->par.mode == SPL_MODE_EA ? 1 : 0) +
+                         (c->par.sched != SPL_SCHED_NONE || c->recording ? 1 : 0) +
+                         (c->par.sched != SPL_SCHED_NONE ? 4 : 0);
     if (c->timing) {
         c->ev_pending[c->ev_set] = true;
         c->ev_set ^= 1;
@@ -655,7 +707,7 @@ extern "C" int spl_render_batch(spl_ctx *c, const spl_camera *cams, int32_t n_vi
     DeviceGuard g(c->device);
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     const unsigned long long key = batch_key(c, cams, n_views);
-    if (c->graph && c->graph_key == key) {
+    if (c->use_graph && c->graph && c->graph_key == key) {
         // replay: stage the constants, launch, check the device-side guards
         Views vs{};
         SPL_TRY(prepare_views(c, cams, n_views, d_images, vs));
@@ -686,6 +738,7 @@ extern "C" int spl_render_batch(spl_ctx *c, const spl_camera *cams, int32_t n_vi
     }
     // eager render (exact list sizes), then capture a graph for the next call
     SPL_TRY(render_views(c, cams, n_views, d_images, s));
+    if (!c->use_graph) return SPL_OK;
     SPL_CUDA(cudaStreamSynchronize(s));
     harvest_timing(c, c->ev_set ^ 1);
     Views vs{};
@@ -693,6 +746,7 @@ extern "C" int spl_render_batch(spl_ctx *c, const spl_camera *cams, int32_t n_vi
     // headroom so that small changes of the cameras still fit the graph
     SPL_TRY(grow(c, c->entries, c->entries.cap + c->entries.cap / 4));
     SPL_TRY(grow(c, c->items, c->items.cap + c->items.cap / 4));
+    SPL_TRY(size_item_buffers(c));
     SPL_TRY(capture_batch(c, vs, batch_key(c, cams, n_views)));
     return SPL_OK;
 }
@@ -752,6 +806,108 @@ extern "C" int spl_autotune(spl_ctx *c, const spl_camera *cams, int32_t n_views,
     if (best) *best = bp;
     if (best_ms) *best_ms = bms;
     return SPL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tile-cost network: model, samples, kernels, training.
+// ---------------------------------------------------------------------------
+extern "C" int spl_set_model(spl_ctx *c, const float *theta, const float *heur) {
+    if (!c) return SPL_EINVAL;
+    DeviceGuard g(c->device);
+    if (theta) {
+        for (int k = 0; k < kNParam; ++k)
+            if (!std::isfinite(theta[k])) return SPL_EINVAL;
+        SPL_CUDA(cudaMemcpy(c->theta.p, theta, sizeof(float) * kNParam, cudaMemcpyHostToDevice));
+        c->have_model = true;
+    }
+    if (heur) {
+        if (!std::isfinite(heur[0]) || !std::isfinite(heur[1])) return SPL_EINVAL;
+        SPL_CUDA(cudaMemcpy(c->heur.p, heur, sizeof(float) * 2, cudaMemcpyHostToDevice));
+    }
+    return SPL_OK;
+}
+
+extern "C" int spl_set_recording(spl_ctx *c, int32_t enable) {
+    if (!c) return SPL_EINVAL;
+    c->recording = enable != 0;
+    return SPL_OK;
+}
+
+extern "C" int spl_get_samples(spl_ctx *c, float *d_feat, float *d_logc, int64_t cap, int64_t *n) {
+    if (!c || !n || cap < 0 || (cap > 0 && (!d_feat || !d_logc))) return SPL_EINVAL;
+    if (!c->recording) return SPL_ESTATE;
+    DeviceGuard g(c->device);
+    SPL_CUDA(cudaStreamSynchronize(c->stream));
+    const int64_t m = c->last_items < cap ? c->last_items : cap;
+    if (m > 0) {
+        SPL_CUDA(cudaMemcpy(d_feat, c->feat.p, sizeof(float) * kFeat * m, cudaMemcpyDeviceToDevice));
+        launch_log_cycles(c->item_cycles.p, m, d_logc, c->stream);
+        SPL_CUDA(cudaGetLastError());
+        SPL_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    *n = m;
+    return SPL_OK;
+}
+
+extern "C" int spl_mlp_nparam(void) { return kNParam; }
+
+extern "C" int spl_mlp_forward(const float *d_theta, const float *d_x, int64_t B, float *d_y,
+                               void *stream) {
+    if (!d_theta || B < 0 || (B > 0 && (!d_x || !d_y))) return SPL_EINVAL;
+    launch_mlp_forward(d_theta, d_x, B, d_y, (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int spl_mlp_loss_grad(const float *d_theta, const float *d_x, const float *d_t, int64_t B,
+                                 float *d_grad, float *d_loss, void *stream) {
+    if (!d_theta || !d_grad || B < 1 || !d_x || !d_t) return SPL_EINVAL;
+    float *work = nullptr;
+    if (cudaMalloc((void **)&work, sizeof(float) * mlp_work_floats(B)) != cudaSuccess) {
+        cudaGetLastError();
+        return SPL_ENOMEM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_mlp_loss_grad(d_theta, d_x, d_t, B, work, d_grad, d_loss, s);
+    int rc = cuda_status(cudaGetLastError());
+    if (rc == SPL_OK) rc = cuda_status(cudaStreamSynchronize(s));
+    cudaFree(work);
+    return rc;
+}
+
+extern "C" int spl_mlp_adam(float *d_theta, const float *d_grad, float *d_m, float *d_v, int64_t np,
+                            int64_t step, float lr, float beta1, float beta2, float eps,
+                            void *stream) {
+    if (!d_theta || !d_grad || !d_m || !d_v || np < 0 || step < 1) return SPL_EINVAL;
+    launch_mlp_adam(d_theta, d_grad, d_m, d_v, np, step, lr, beta1, beta2, eps, (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int spl_mlp_train(const float *d_x, const float *d_t, int64_t B, float *theta,
+                             int32_t steps, float lr, float *losses, void *stream) {
+    if (!d_x || !d_t || B < 1 || !theta || steps < 0 || !(lr > 0.f)) return SPL_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *buf = nullptr;
+    const size_t nf = 4 * (size_t)kNParam + (size_t)(steps + 1) + mlp_work_floats(B);
+    if (cudaMalloc((void **)&buf, sizeof(float) * nf) != cudaSuccess) {
+        cudaGetLastError();
+        return SPL_ENOMEM;
+    }
+    float *th = buf, *gr = th + kNParam, *m = gr + kNParam, *v = m + kNParam;
+    float *ls = v + kNParam, *work = ls + steps + 1;
+    int rc = cuda_status(cudaMemcpyAsync(th, theta, sizeof(float) * kNParam, cudaMemcpyHostToDevice, s));
+    if (rc == SPL_OK) rc = cuda_status(cudaMemsetAsync(m, 0, sizeof(float) * 2 * kNParam, s));
+    for (int k = 0; rc == SPL_OK && k < steps; ++k) {
+        launch_mlp_loss_grad(th, d_x, d_t, B, work, gr, ls + k, s);
+        launch_mlp_adam(th, gr, m, v, kNParam, k + 1, lr, 0.9f, 0.999f, 1e-8f, s);
+    }
+    if (rc == SPL_OK) rc = cuda_status(cudaGetLastError());
+    if (rc == SPL_OK) rc = cuda_status(cudaMemcpyAsync(theta, th, sizeof(float) * kNParam,
+                                                       cudaMemcpyDeviceToHost, s));
+    if (rc == SPL_OK && losses && steps > 0)
+        rc = cuda_status(cudaMemcpyAsync(losses, ls, sizeof(float) * steps, cudaMemcpyDeviceToHost, s));
+    if (rc == SPL_OK) rc = cuda_status(cudaStreamSynchronize(s));
+    cudaFree(buf);
+    return rc;
 }
 
 extern "C" int spl_get_records(spl_ctx *c, int64_t n, double *xs, double *ys, float *r, float *e,

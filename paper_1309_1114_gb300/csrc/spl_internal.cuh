@@ -126,7 +126,14 @@ struct TileArgs {
     int items_cap;
     float *const *images;      // device array: one image per view
     DevStats *st;
+    const int *order;          // optional: processing order of each pass's items
+    long long *item_cycles;    // optional: SM clock cycles spent on each item
 };
+
+// Tile-cost network 32 -> 64 (ReLU) -> 1; parameter vector layout
+// W1[64][32] row-major, b1[64], w2[64], b2.
+constexpr int kFeat = 32, kHid = 64;
+constexpr int kNParam = kHid * kFeat + 2 * kHid + 1;
 
 // Launchers (stream-ordered, no synchronisation).  Every count the kernels
 // need after binning (entries, work items) is read from device memory, so
@@ -154,6 +161,26 @@ void launch_zero_images(const Views &v, float *const *images, int sms, cudaStrea
 void launch_epilogue_views(const Views &v, float *const *images, int sms, cudaStream_t s);
 void launch_count_work(const FrameConst &fc, const float4 *rec0, const float4 *rec1, int64_t n,
                        unsigned long long *work, int sms, cudaStream_t s);
+
+// Scheduling of the work items (spl_sched.cu): per-item features, predicted
+// cost (network or count heuristic), and a longest-first order per pass.
+void launch_item_features(const Views &v, const TileArgs &a, float area_scale, int max_sample,
+                          float *feat, int *n_entries, int sms, cudaStream_t s);
+void launch_item_cost(const float *feat, const int *n_entries, const float *theta,
+                      const float *heur, int items_cap, const DevStats *st, float *cost,
+                      cudaStream_t s);
+void launch_order_items(const float *cost, int items_cap, DevStats *st, int *hist, int *order,
+                        cudaStream_t s);
+
+// Network kernels (spl_mlp.cu); B samples, features row-major [B][32].
+void launch_mlp_forward(const float *theta, const float *x, int64_t B, float *y, cudaStream_t s);
+void launch_mlp_loss_grad(const float *theta, const float *x, const float *t, int64_t B,
+                          float *work, float *grad, float *loss, cudaStream_t s);
+void launch_mlp_adam(float *theta, const float *grad, float *m, float *v, int64_t np, int64_t step,
+                     float lr, float b1, float b2, float eps, cudaStream_t s);
+size_t mlp_work_floats(int64_t B);
+// logc[k] = log(cycles[k]) (cycles clamped to >= 1).
+void launch_log_cycles(const long long *cycles, int64_t n, float *logc, cudaStream_t s);
 
 // View of a global tile index (binary search over the views' tile bases).
 __device__ __forceinline__ int view_of_tile(const FrameConst *fcs, int nviews, int g) {

@@ -230,8 +230,10 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
         __syncthreads();
         const int it = s_item;
         if (it >= n_items) break;
-        const WorkItem w = a.items[item0 + it];
+        const int idx = item0 + (a.order ? a.order[item0 + it] : it);
+        const WorkItem w = a.items[idx];
         const int view = item_view(w), list = item_list(w);
+        const long long t_start = clock64();
         {
             const int words = (int)(sizeof(FrameConst) / sizeof(int));
             if (tid < words)
@@ -346,6 +348,10 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
                         atomicAdd(dst + c, v);
                 }
             }
+        }
+        if (a.item_cycles) {
+            __syncthreads();
+            if (tid == 0) a.item_cycles[idx] = clock64() - t_start;
         }
     }
 }

@@ -21,6 +21,7 @@ SPL_MEM_HOST, SPL_MEM_DEVICE = 0, 1
 SPL_ATTR_F32, SPL_ATTR_F16, SPL_ATTR_F16_IS = 0, 1, 2
 SPL_MODE_ADDITIVE, SPL_MODE_EA = 0, 1
 SPL_SCHED_NONE, SPL_SCHED_COUNT, SPL_SCHED_MLP = 0, 1, 2
+SPL_MLP_NPARAM = 2177
 
 
 class spl_particles(C.Structure):
@@ -72,8 +73,18 @@ _SIGS = {
     "spl_render_batch": [_P, C.POINTER(spl_camera), C.c_int32, C.POINTER(C.c_void_p), _P],
     "spl_get_stats": [_P, C.POINTER(spl_stats)],
     "spl_set_timing": [_P, C.c_int32],
+    "spl_set_graph": [_P, C.c_int32],
     "spl_get_records": [_P, C.c_int64, _P, _P, _P, _P, _P],
     "spl_count_work": [_P, C.POINTER(C.c_int64)],
+    "spl_set_model": [_P, _P, _P],
+    "spl_set_recording": [_P, C.c_int32],
+    "spl_get_samples": [_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)],
+    "spl_mlp_nparam": [],
+    "spl_mlp_forward": [_P, _P, C.c_int64, _P, _P],
+    "spl_mlp_loss_grad": [_P, _P, _P, C.c_int64, _P, _P, _P],
+    "spl_mlp_adam": [_P, _P, _P, _P, C.c_int64, C.c_int64, C.c_float, C.c_float, C.c_float,
+                     C.c_float, _P],
+    "spl_mlp_train": [_P, _P, C.c_int64, _P, C.c_int32, C.c_float, _P, _P],
     "spl_autotune": [_P, C.POINTER(spl_camera), C.c_int32, C.POINTER(C.c_void_p), C.c_int32,
                      C.POINTER(spl_params), C.POINTER(C.c_float)],
     "spl_render_noalloc": [C.POINTER(spl_particles), C.POINTER(spl_camera), C.POINTER(spl_params),
@@ -225,6 +236,9 @@ class Renderer:
     def set_timing(self, on: bool = True):
         check(load_library().spl_set_timing(self._h, int(bool(on))), "spl_set_timing")
 
+    def set_graph(self, on: bool = True):
+        check(load_library().spl_set_graph(self._h, int(bool(on))), "spl_set_graph")
+
     def render(self, image, stream: int | None = None):
         check(load_library().spl_render(self._h, image.data_ptr(), stream), "spl_render")
         return image
@@ -253,6 +267,24 @@ class Renderer:
         check(load_library().spl_autotune(self._h, arr, len(cams), ptrs, int(reps), C.byref(best),
                                           C.byref(ms)), "spl_autotune")
         return {k: getattr(best, k) for k, _ in best._fields_}, float(ms.value)
+
+    def set_model(self, theta=None, heur=None):
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+        hu = None if heur is None else np.ascontiguousarray(heur, dtype=np.float32)
+        if th is not None and th.size != SPL_MLP_NPARAM:
+            raise ValueError("theta must hold SPL_MLP_NPARAM floats")
+        check(load_library().spl_set_model(self._h, None if th is None else th.ctypes.data,
+                                           None if hu is None else hu.ctypes.data), "spl_set_model")
+
+    def set_recording(self, on: bool = True):
+        check(load_library().spl_set_recording(self._h, int(bool(on))), "spl_set_recording")
+
+    def samples(self, feat, logc) -> int:
+        """Copy the last render's item samples into CUDA tensors; returns the count."""
+        n = C.c_int64(0)
+        check(load_library().spl_get_samples(self._h, feat.data_ptr(), logc.data_ptr(),
+                                             int(logc.numel()), C.byref(n)), "spl_get_samples")
+        return int(n.value)
 
     def stats(self) -> dict:
         s = spl_stats()

@@ -280,3 +280,11 @@ def test_tile_features_hand_counted():
         assert nz[t][3] == pytest.approx(math.log1p(1.0))
         assert nz[t][16 + 3] == pytest.approx(math.log1p(a))
         assert np.count_nonzero(nz[t]) == 2
+
+
+def test_tile_membership_needs_the_disc_not_just_the_box():
+    cam = axis_camera(64)                     # f = 32, 16 px tiles -> 4 x 4
+    # x_s = y_s = 8 (centre of tile 0), r = 9: the box reaches tiles 0, 1, 4, 5,
+    # but the nearest pixel centre of tile 5, (16.5, 16.5), is 8.5 sqrt(2) > 9 away
+    f = oracle.tile_features(parts_of([0.75, 0.75, 1.0, 9.0 / 96.0, 1.0, 0.0]), CONST_PAL, cam, {}, 16)
+    assert sorted(np.nonzero(f[:, :16].sum(1))[0].tolist()) == [0, 1, 4]
