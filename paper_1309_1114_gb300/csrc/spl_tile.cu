@@ -42,15 +42,17 @@ namespace spl {
 
 template <int T>
 struct Shape {
-    static constexpr int TC = T < 32 ? T : 32;     // distinct columns per warp instruction
-    static constexpr int G = 32 / TC;              // lane groups (rows split between them)
-    static constexpr int CPL = T / TC;             // columns per lane
-    static constexpr int RPW = T / 8;              // rows per warp (8 warps)
-    static constexpr int RPL = RPW / G;            // rows per lane
+    // A tile is cut into 8 row bands, one per warp: BW columns x BH rows.
+    static constexpr int BW = T == 64 ? 64 : 16;
+    static constexpr int BH = T * T / (8 * BW);
+    static constexpr int NBX = T / BW;             // bands across the tile
+    static constexpr int LW = BW < 32 ? BW : 32;   // lanes along a band row
+    static constexpr int G = 32 / LW;              // lane groups (rows split between them)
+    static constexpr int CPL = BW / LW;            // columns per lane
+    static constexpr int RPL = BH / G;             // rows per lane
     static constexpr int P = 32;                   // particles per tabulated batch
     static constexpr int PER = T / 8;              // table columns (and rows) per thread
 };
-
 
 // One small particle into the shared tile: the warp spreads the particle's
 // pixel box (inside the tile) over its lanes, so no two lanes of a warp touch
@@ -125,9 +127,9 @@ __device__ __forceinline__ void warp_points(const TileArgs &a, const float4 *s0,
 // swx[p][c] = (w_x, dx^2 B) for tile column c, srow[p][j] = (e w_y, (r^2 -
 // dy^2) B + 1) for tile row j.  Thread (p, q) = (tid / 8, tid % 8) fills
 // columns and rows q, q + 8, q + 16, ... of particle p (consecutive lanes
-// write consecutive table entries, free of bank conflicts), and decides for
-// row band q whether the disc reaches it (bit p of band_mask[q]) and whether
-// it covers the whole band (bit p of full_mask[q]).
+// write consecutive table entries, free of bank conflicts).  The thread also
+// decides for row band q whether the disc reaches it (bit p of band_mask[q])
+// and whether it covers the whole band (bit p of full_mask[q]).
 template <int T>
 __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, int cnt, int x0,
                                          int y0, float2 (*swx)[T], float4 (*srow)[T],
@@ -140,6 +142,12 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
     const float B = 1048576.f / r2;
     const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
     const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
+    // the particle's box in tile coordinates (conservative by 1e-3 px)
+    const float r = sqrtf(r2) + 1e-3f;
+    const int ilo = xi - x0 + (int)ceilf(fmaxf(r0.y - 0.5f - r, -1e6f));
+    const int ihi = xi - x0 + (int)floorf(fminf(r0.y - 0.5f + r, 1e6f));
+    const int jlo = yi - y0 + (int)ceilf(fmaxf(r0.z - 0.5f - r, -1e6f));
+    const int jhi = yi - y0 + (int)floorf(fminf(r0.z - 0.5f + r, 1e6f));
 #pragma unroll
     for (int u = 0; u < S::PER; ++u) {
         const int k = q + 8 * u;
@@ -151,15 +159,13 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
         const float wy = ex2_neg(kq * dy2);
         srow[p][k] = make_float4(r1.y * wy, r1.z * wy, r1.w * wy, fmaf(r2 - dy2, B, 1.f));
     }
-    // row band q = rows [q RPW, (q+1) RPW) of the tile (the rows of warp q)
-    const float r = sqrtf(r2) + 1e-3f;
-    const int jlo = yi - y0 + (int)ceilf(fmaxf(r0.z - 0.5f - r, -1e6f));
-    const int jhi = yi - y0 + (int)floorf(fminf(r0.z - 0.5f + r, 1e6f));
-    const int b0 = q * S::RPW, b1 = b0 + S::RPW - 1;
-    if (jhi >= b0 && jlo <= b1) {
+    // row band q: columns [bx BW, bx BW + BW), rows [by BH, by BH + BH)
+    const int bx0 = (q % S::NBX) * S::BW, by0 = (q / S::NBX) * S::BH;
+    const int bx1 = bx0 + S::BW - 1, by1 = by0 + S::BH - 1;
+    if (jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1) {
         atomicOr(&band_mask[q], 1u << p);
-        const float dxa = (float)(x0 - xi) + xh, dxb = (float)(x0 + T - 1 - xi) + xh;
-        const float dya = (float)(y0 + b0 - yi) + yh, dyb = (float)(y0 + b1 - yi) + yh;
+        const float dxa = (float)(x0 + bx0 - xi) + xh, dxb = (float)(x0 + bx1 - xi) + xh;
+        const float dya = (float)(y0 + by0 - yi) + yh, dyb = (float)(y0 + by1 - yi) + yh;
         if (fmaxf(dya * dya, dyb * dyb) + fmaxf(dxa * dxa, dxb * dxb) <= r2 * (1.f - 4e-6f))
             atomicOr(&full_mask[q], 1u << p);
     }
@@ -256,7 +262,8 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
         } else {
             lb2 = w.start; le2 = w.end;      // medium (tile pass) or large (large pass)
         }
-        const int col = lane % S::TC, row0 = warp * S::RPW + (lane / S::TC) * S::RPL;
+        const int col = (warp % S::NBX) * S::BW + lane % S::LW;
+        const int row0 = (warp / S::NBX) * S::BH + (lane / S::LW) * S::RPL;
         float acc[S::RPL][S::CPL][3];
 #pragma unroll
         for (int q = 0; q < S::RPL; ++q)
