@@ -35,7 +35,8 @@
  *     y_s = H/2 - f y_c/z_c (y grows downwards); pixel (i,j) has its centre
  *     at (i+1/2, j+1/2); sigma_s = sigma_p f / (z_c S_box); r = chi sigma_s;
  *   - inactive iff z_c <= z_near or the box [x_s-r,x_s+r]x[y_s-r,y_s+r]
- *     misses [0,W)x[0,H);
+ *     misses [0,W)x[0,H); a particle with a non-finite input (x, y, z, h, I,
+ *     s) or a negative smoothing length is inactive as well;
  *   - palette: s' = clamp((s-s_min)/(s_max-s_min),0,1), u = s'(n-1),
  *     k = min(floor(u), n-2), colour = pal[k] + (u-k)(pal[k+1]-pal[k]);
  *     emission e = brightness * I * colour (I plays rho0 of Eq. 2);
@@ -155,6 +156,9 @@ static void project_one(const orc_view *v, const orc_params *q, const float *pal
     o->cls = ORC_INACTIVE;
     o->xs = o->ys = o->sigma = o->r = 0.0;
     o->e[0] = o->e[1] = o->e[2] = 0.0;
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(hh) || !isfinite(inten) ||
+        !isfinite(sc) || hh < 0.0)
+        return;
     if (!(zc > v->z_near)) return;
     o->xs = v->half_w + v->f * xc / zc;
     o->ys = v->half_h - v->f * yc / zc;

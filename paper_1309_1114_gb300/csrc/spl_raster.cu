@@ -88,6 +88,10 @@ __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spa
     }
     r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
+    // non-finite inputs or a negative smoothing length: inactive
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(h) || !isfinite(inten) ||
+        !isfinite(s) || h < 0.f)
+        return CLS_INACTIVE;
     const float zc = c[2].hi;
     if (!(zc > fc.z_near)) return CLS_INACTIVE;
     // perspective projection

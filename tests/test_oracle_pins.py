@@ -288,3 +288,14 @@ def test_tile_membership_needs_the_disc_not_just_the_box():
     # but the nearest pixel centre of tile 5, (16.5, 16.5), is 8.5 sqrt(2) > 9 away
     f = oracle.tile_features(parts_of([0.75, 0.75, 1.0, 9.0 / 96.0, 1.0, 0.0]), CONST_PAL, cam, {}, 16)
     assert sorted(np.nonzero(f[:, :16].sum(1))[0].tolist()) == [0, 1, 4]
+
+
+def test_non_finite_or_negative_inputs_are_inactive():
+    cam = axis_camera(64)
+    nan, inf = float("nan"), float("inf")
+    rows = [[nan, 0.0, 1.0, 0.01, 1, 0], [0.0, 0.0, inf, 0.01, 1, 0], [0.0, 0.0, 1.0, nan, 1, 0],
+            [0.0, 0.0, 1.0, 0.01, inf, 0], [0.0, 0.0, 1.0, 0.01, 1, nan], [0.0, 0.0, 1.0, -0.01, 1, 0]]
+    rec = oracle.project(parts_of(rows), CONST_PAL, cam)
+    assert list(rec["cls"]) == [-2] * 6
+    img = oracle.render(parts_of(rows + [[0.0, 0.0, 1.0, 0.05, 1.0, 0.0]]), CONST_PAL, cam)
+    assert np.isfinite(img).all() and img.max() > 0
