@@ -24,6 +24,8 @@
 //     then every warp whose row band the particle reaches adds
 //     e * w_y * w_x into its registers: three FMAs per pixel, plus a clip
 //     test folded into one saturating add on the FMA pipe (see below);
+//     where a lane holds an even number of rows, two rows go through one
+//     packed FP32x2 instruction (the row table is laid out in row pairs);
 //   - finally each thread adds the shared-memory part to its registers and
 //     writes its pixels once.
 // The large pass (r > r_large, Sec. 4.3) runs after the tile pass with the
@@ -52,6 +54,58 @@ struct Shape {
     static constexpr int RPL = BH / G;             // rows per lane
     static constexpr int P = 32;                   // particles per tabulated batch
     static constexpr int PER = T / 8;              // table columns (and rows) per thread
+    static constexpr bool PAIRED = RPL % 2 == 0;   // rows two at a time (FP32x2)
+};
+
+// Two FP32 values in one 64-bit register pair: the operand of the packed
+// FP32x2 multiply and FMA (each half rounded as the scalar instruction).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ void fma2(f32x2 &acc, f32x2 a, f32x2 b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+// The registers of one thread's pixels: RPL rows x CPL columns x RGB, held
+// as row pairs when the rows are processed two at a time.
+template <int T, bool PAIRED = Shape<T>::PAIRED>
+struct Acc {
+    using S = Shape<T>;
+    float v[S::RPL][S::CPL][3];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < S::RPL; ++q)
+#pragma unroll
+            for (int k = 0; k < S::CPL; ++k) v[q][k][0] = v[q][k][1] = v[q][k][2] = 0.f;
+    }
+    __device__ __forceinline__ float get(int q, int k, int c) const { return v[q][k][c]; }
+};
+template <int T>
+struct Acc<T, true> {
+    using S = Shape<T>;
+    f32x2 v[S::RPL / 2][S::CPL][3];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < S::RPL / 2; ++q)
+#pragma unroll
+            for (int k = 0; k < S::CPL; ++k) v[q][k][0] = v[q][k][1] = v[q][k][2] = 0ull;
+    }
+    __device__ __forceinline__ float get(int q, int k, int c) const {
+        float lo, hi;
+        unpack2(v[q >> 1][k][c], lo, hi);
+        return (q & 1) ? hi : lo;
+    }
 };
 
 // One small particle into the shared tile: the warp spreads the particle's
@@ -124,22 +178,26 @@ __device__ __forceinline__ void warp_points(const TileArgs &a, const float4 *s0,
 }
 
 // Tabulate the separable factors of a batch of cnt <= 32 staged particles:
-// swx[p][c] = (w_x, dx^2 B) for tile column c, srow[p][j] = (e w_y, (r^2 -
-// dy^2) B + 1) for tile row j.  Thread (p, q) = (tid / 8, tid % 8) fills
-// columns and rows q, q + 8, q + 16, ... of particle p (consecutive lanes
-// write consecutive table entries, free of bank conflicts).  The thread also
-// decides for row band q whether the disc reaches it (bit p of band_mask[q])
-// and whether it covers the whole band (bit p of full_mask[q]).
+// swx[p][c] = (w_x, dx^2 B) for tile column c; for tile row j the row terms
+// e_R w_y, e_G w_y, e_B w_y and (r^2 - dy^2) B + 1.  Rows are stored one
+// float4 per row, or -- when the rows go two at a time -- per row pair
+// (2m, 2m+1) as srow[p][2m] = (e_R w_y, same for row 2m+1, e_G w_y, e_G w_y')
+// and srow[p][2m+1] = (e_B w_y, e_B w_y', rem, rem'), so that every packed
+// operand is one aligned half of a 16-byte load.  Thread (p, q) = (tid / 8,
+// tid % 8) fills columns q, q + 8, q + 16, ... (and the same rows, or row
+// pairs q, q + 8, ...) of particle p.  It also decides for row band q whether
+// the disc reaches it (bit p of band_mask[q]).  B only needs to be the same
+// on both sides of the clip test, so a fast reciprocal serves.
 template <int T>
 __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, int cnt, int x0,
                                          int y0, float2 (*swx)[T], float4 (*srow)[T],
-                                         unsigned *band_mask, unsigned *full_mask, int tid) {
+                                         unsigned *band_mask, int tid) {
     using S = Shape<T>;
     const int p = tid >> 3, q = tid & 7;
     if (p >= cnt) return;
     const float4 r0 = st0[p], r1 = st1[p];
     const float kq = r0.w, r2 = r1.x;
-    const float B = 1048576.f / r2;
+    const float B = __fdividef(1048576.f, r2);
     const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
     const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
     // the particle's box in tile coordinates (conservative by 1e-3 px)
@@ -154,27 +212,39 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
         const float dx = (float)(x0 + k - xi) + xh;
         const float dx2 = dx * dx;
         swx[p][k] = make_float2(ex2_neg(kq * dx2), dx2 * B);
-        const float dy = (float)(y0 + k - yi) + yh;
-        const float dy2 = dy * dy;
-        const float wy = ex2_neg(kq * dy2);
-        srow[p][k] = make_float4(r1.y * wy, r1.z * wy, r1.w * wy, fmaf(r2 - dy2, B, 1.f));
+    }
+    if constexpr (S::PAIRED) {
+#pragma unroll
+        for (int u = 0; u < S::PER / 2; ++u) {
+            const int m = q + 8 * u;
+            const float dya = (float)(y0 + 2 * m - yi) + yh, dyb = (float)(y0 + 2 * m + 1 - yi) + yh;
+            const float a2 = dya * dya, b2 = dyb * dyb;
+            const float wa = ex2_neg(kq * a2), wb = ex2_neg(kq * b2);
+            srow[p][2 * m] = make_float4(r1.y * wa, r1.y * wb, r1.z * wa, r1.z * wb);
+            srow[p][2 * m + 1] =
+                make_float4(r1.w * wa, r1.w * wb, fmaf(r2 - a2, B, 1.f), fmaf(r2 - b2, B, 1.f));
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < S::PER; ++u) {
+            const int k = q + 8 * u;
+            const float dy = (float)(y0 + k - yi) + yh;
+            const float dy2 = dy * dy;
+            const float wy = ex2_neg(kq * dy2);
+            srow[p][k] = make_float4(r1.y * wy, r1.z * wy, r1.w * wy, fmaf(r2 - dy2, B, 1.f));
+        }
     }
     // row band q: columns [bx BW, bx BW + BW), rows [by BH, by BH + BH)
     const int bx0 = (q % S::NBX) * S::BW, by0 = (q / S::NBX) * S::BH;
     const int bx1 = bx0 + S::BW - 1, by1 = by0 + S::BH - 1;
-    if (jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1) {
-        atomicOr(&band_mask[q], 1u << p);
-        const float dxa = (float)(x0 + bx0 - xi) + xh, dxb = (float)(x0 + bx1 - xi) + xh;
-        const float dya = (float)(y0 + by0 - yi) + yh, dyb = (float)(y0 + by1 - yi) + yh;
-        if (fmaxf(dya * dya, dyb * dyb) + fmaxf(dxa * dxa, dxb * dxb) <= r2 * (1.f - 4e-6f))
-            atomicOr(&full_mask[q], 1u << p);
-    }
+    if (jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1) atomicOr(&band_mask[q], 1u << p);
 }
 
-// Add tabulated particle p into the registers of this thread's pixels.
-template <int T, bool FULL>
+// Add tabulated particle p into the registers of this thread's pixels.  The
+// clip factor is exactly 1 inside the disc and 0 outside (see the top).
+template <int T>
 __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp, int col, int row0,
-                                           float (&acc)[Shape<T>::RPL][Shape<T>::CPL][3]) {
+                                           Acc<T, false> &acc) {
     using S = Shape<T>;
     float wx[S::CPL], dxb[S::CPL];
 #pragma unroll
@@ -188,11 +258,40 @@ __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp
         const float4 rv = rowp[row0 + q];
 #pragma unroll
         for (int k = 0; k < S::CPL; ++k) {
-            // clip factor: exactly 1 inside the disc, 0 outside (see the top)
-            const float wk = FULL ? wx[k] : wx[k] * __saturatef(rv.w - dxb[k]);
-            acc[q][k][0] = fmaf(rv.x, wk, acc[q][k][0]);
-            acc[q][k][1] = fmaf(rv.y, wk, acc[q][k][1]);
-            acc[q][k][2] = fmaf(rv.z, wk, acc[q][k][2]);
+            const float wk = wx[k] * __saturatef(rv.w - dxb[k]);
+            acc.v[q][k][0] = fmaf(rv.x, wk, acc.v[q][k][0]);
+            acc.v[q][k][1] = fmaf(rv.y, wk, acc.v[q][k][1]);
+            acc.v[q][k][2] = fmaf(rv.z, wk, acc.v[q][k][2]);
+        }
+    }
+}
+
+// The same two rows at a time: per row pair two 16-byte loads, two scalar
+// clips, one packed multiply and three packed FMAs (R, G, B of both rows).
+template <int T>
+__device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp, int col, int row0,
+                                           Acc<T, true> &acc) {
+    using S = Shape<T>;
+    float dxb[S::CPL];
+    f32x2 ww[S::CPL];
+#pragma unroll
+    for (int k = 0; k < S::CPL; ++k) {
+        const float2 v = wxp[col + 32 * k];
+        ww[k] = pack2(v.x, v.x);
+        dxb[k] = v.y;
+    }
+    const ulonglong2 *rp = reinterpret_cast<const ulonglong2 *>(rowp) + row0;
+#pragma unroll
+    for (int m = 0; m < S::RPL / 2; ++m) {
+        const ulonglong2 a = rp[2 * m], b = rp[2 * m + 1];
+        float ra, rb;
+        unpack2(b.y, ra, rb);
+#pragma unroll
+        for (int k = 0; k < S::CPL; ++k) {
+            const f32x2 w = mul2(pack2(__saturatef(ra - dxb[k]), __saturatef(rb - dxb[k])), ww[k]);
+            fma2(acc.v[m][k][0], a.x, w);
+            fma2(acc.v[m][k][1], a.y, w);
+            fma2(acc.v[m][k][2], b.x, w);
         }
     }
 }
@@ -222,7 +321,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
     float4 *st1 = st0 + kTileThreads;
     float2 (*swx)[T] = reinterpret_cast<float2 (*)[T]>(st1 + kTileThreads);
     float (*sacc)[T][T] = reinterpret_cast<float (*)[T][T]>(&swx[S::P][0]);
-    __shared__ unsigned band_mask[NW], full_mask[NW];
+    __shared__ unsigned band_mask[NW];
     __shared__ int s_item;
     __shared__ FrameConst sfc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -264,11 +363,8 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
         }
         const int col = (warp % S::NBX) * S::BW + lane % S::LW;
         const int row0 = (warp / S::NBX) * S::BH + (lane / S::LW) * S::RPL;
-        float acc[S::RPL][S::CPL][3];
-#pragma unroll
-        for (int q = 0; q < S::RPL; ++q)
-#pragma unroll
-            for (int k = 0; k < S::CPL; ++k) acc[q][k][0] = acc[q][k][1] = acc[q][k][2] = 0.f;
+        Acc<T> acc;
+        acc.zero();
 
         // points (Sec. 4.1): batches of 256 staged records, warp-aggregated
 #pragma unroll 1
@@ -312,25 +408,21 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
                 st0[tid] = n0;
                 st1[tid] = n1;
             }
-            if (tid < NW) band_mask[tid] = full_mask[tid] = 0u;
+            if (tid < NW) band_mask[tid] = 0u;
             __syncthreads();
             if (base + S::P + tid < le2 && tid < S::P) {
                 const unsigned id = a.entries[base + S::P + tid];
                 n0 = a.rec0[id];
                 n1 = a.rec1[id];
             }
-            tabulate<T>(st0, st1, cnt, x0, y0, swx, srow, band_mask, full_mask, tid);
+            tabulate<T>(st0, st1, cnt, x0, y0, swx, srow, band_mask, tid);
             __syncthreads();
             // this warp's row band: only the particles that reach it
             unsigned mask = band_mask[warp];
-            const unsigned fullm = full_mask[warp];
             while (mask) {
                 const int p = __ffs(mask) - 1;
                 mask &= mask - 1u;
-                if ((fullm >> p) & 1u)
-                    band_splat<T, true>(swx[p], srow[p], col, row0, acc);
-                else
-                    band_splat<T, false>(swx[p], srow[p], col, row0, acc);
+                band_splat<T>(swx[p], srow[p], col, row0, acc);
             }
             __syncthreads();
         }
@@ -348,7 +440,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
                 float *dst = image + 3 * ((int64_t)(y0 + row) * fc.width + x0 + cx);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float v = sacc[c][row][cx] + acc[q][k][c];
+                    const float v = sacc[c][row][cx] + acc.get(q, k, c);
                     if (store)
                         dst[c] = v;
                     else if (v != 0.f)
