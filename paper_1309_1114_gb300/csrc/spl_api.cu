@@ -144,7 +144,7 @@ extern "C" int spl_default_params(spl_params *q) {
     q->r_sml = 0.5;
     q->brightness = 1.0;
     q->tile_px = 32;
-    q->r_small = 4.0;
+    q->r_small = 0.5;
     q->r_large = 64.0;
     q->mode = SPL_MODE_ADDITIVE;
     q->sched = SPL_SCHED_NONE;
@@ -764,7 +764,7 @@ extern "C" int spl_autotune(spl_ctx *c, const spl_camera *cams, int32_t n_views,
     if (!c->have_particles || c->npal < 1) return SPL_ESTATE;
     DeviceGuard g(c->device);
     static const int tiles[] = {16, 32, 64};
-    static const double radii[][2] = {{2.0, 32.0}, {4.0, 64.0}, {8.0, 128.0}, {4.0, 1e9}};
+    static const double radii[][2] = {{0.0, 32.0}, {0.0, 64.0}, {0.0, 128.0}, {0.0, 1e9}, {2.0, 64.0}};
     const spl_params base = c->par;
     spl_params bp = base;
     float bms = -1.f;

@@ -201,7 +201,7 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
     const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
     const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
     // the particle's box in tile coordinates (conservative by 1e-3 px)
-    const float r = sqrtf(r2) + 1e-3f;
+    const float r = r2 * rsqrtf(r2) + 1e-3f;   // approximate: far inside the margin
     const int ilo = xi - x0 + (int)ceilf(fmaxf(r0.y - 0.5f - r, -1e6f));
     const int ihi = xi - x0 + (int)floorf(fminf(r0.y - 0.5f + r, 1e6f));
     const int jlo = yi - y0 + (int)ceilf(fmaxf(r0.z - 0.5f - r, -1e6f));

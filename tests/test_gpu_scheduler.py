@@ -98,12 +98,13 @@ def test_adam_step_matches_oracle(torch_cuda):
 
 
 def test_item_features_match_oracle_tile_features(rnd, torch_cuda):
-    # few enough particles that no tile is split; no large class
+    # few enough particles that no tile is split (small particles in their own
+    # list, which holds twice as many entries per item); no large class
     sc = scenes.make("uniform", n=20_000, width=320)
     cam = sc.cams[0]
     rnd.load(sc.parts)
     rnd.set_colormap(sc.palette)
-    rnd.set_params(r_large=1e9)
+    rnd.set_params(r_small=4.0, r_large=1e9)
     rnd.set_camera(cam)
     rnd.set_recording(True)
     img = torch_cuda.empty((cam["height"], cam["width"], 3), device="cuda")
