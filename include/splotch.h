@@ -159,6 +159,28 @@ int spl_render(spl_ctx *ctx, float *d_image, void *stream);
  * to h_image (width*height*3 floats); returns when the copy has completed. */
 int spl_render_host(spl_ctx *ctx, float *h_image);
 
+/* Out-of-core render (Sec. 3.2, Eq. 3: a data set larger than device memory
+ * is split into chunks that pass through the device one after the other).
+ * p: particles in HOST memory (p->mem_space must be SPL_MEM_HOST; page-locked
+ * memory lets the copies overlap the rendering), any count n >= 0, FP32 or
+ * FP16 attributes as for spl_load_particles.  chunk >= 1 particles per chunk;
+ * the device holds two chunks of attributes at a time (24 B per particle in
+ * FP32) plus the per-frame scratch of one chunk.  Chunk k+1 is copied on a
+ * second stream while chunk k is rendered on `stream` (NULL: the context
+ * stream); every chunk adds its additive image into d_image (device,
+ * width*height*3 FP32, caller-owned, overwritten), which is exact because
+ * the additive form is linear in the particle set (Sec. 2); the E=A map, if
+ * selected, is applied once after the last chunk.  Camera, colour map and
+ * parameters are the context's; the particles of spl_load_particles are
+ * neither read nor changed.  spl_get_stats then reports the counts summed
+ * over the chunks and the last chunk's tile count.  Returns SPL_EINVAL for bad
+ * arguments or device-memory particles, SPL_ESTATE without a camera or colour
+ * map, SPL_ENOMEM if the chunk buffers do not fit; returns after every copy
+ * has completed (the host arrays may be freed), with the last chunk's
+ * kernels queued on the stream. */
+int spl_render_stream(spl_ctx *ctx, const spl_particles *p, int64_t chunk, float *d_image,
+                      void *stream);
+
 /* Render n_views (1 .. 64) cameras of the loaded particle set in one batch;
  * d_images[k] (device) receives cams[k].width * cams[k].height * 3 floats.
  * The particles are rasterised for every view by one launch (each particle

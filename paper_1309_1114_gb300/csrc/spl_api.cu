@@ -60,6 +60,19 @@ struct spl_ctx {
     bool have_particles = false;
     DevBuf<float> x, y, z;
     DevBuf<unsigned char> h, I, s;
+    // out-of-core rendering (spl_render_stream): two device chunks, filled on
+    // a copy stream; while a chunk renders, the pipeline reads it instead of
+    // the loaded SoA and adds into the image
+    DevBuf<float> cx[2], cy[2], cz[2];
+    DevBuf<unsigned char> ch[2], cI[2], cs[2];
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copied[2] = {}, consumed[2] = {};
+    bool streaming = false;
+    int chunk_buf = 0;
+    int64_t chunk_n = 0;
+    int chunk_attr = SPL_ATTR_F32;
+    bool accumulate = false;      // the image already holds earlier chunks
+    bool last_chunk = true;       // apply the E=A map after this render
     // colour map
     DevBuf<float> pal;
     int npal = 0;
@@ -228,6 +241,13 @@ extern "C" int spl_destroy(spl_ctx *c) {
     else cudaDeviceSynchronize();
     c->x.release(); c->y.release(); c->z.release();
     c->h.release(); c->I.release(); c->s.release();
+    for (int b = 0; b < 2; ++b) {
+        c->cx[b].release(); c->cy[b].release(); c->cz[b].release();
+        c->ch[b].release(); c->cI[b].release(); c->cs[b].release();
+        if (c->copied[b]) cudaEventDestroy(c->copied[b]);
+        if (c->consumed[b]) cudaEventDestroy(c->consumed[b]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     c->pal.release();
     c->rec0.release(); c->rec1.release();
     c->counts.release(); c->offsets.release(); c->cursor.release();
@@ -443,6 +463,10 @@ static int grow(spl_ctx *c, DevBuf<T> &b, size_t n) {
     return b.ensure(n);
 }
 
+// Number of particles the pipeline reads: the loaded set, or the chunk being
+// streamed.
+static int64_t src_n(const spl_ctx *c) { return c->streaming ? c->chunk_n : c->n; }
+
 // Per-view constants into the pinned staging; sizes every per-batch buffer
 // that does not depend on the binning results.
 static int prepare_views(spl_ctx *c, const spl_camera *cams, int V, float *const *images,
@@ -454,14 +478,14 @@ static int prepare_views(spl_ctx *c, const spl_camera *cams, int V, float *const
         fc.view = v;
         fc.tile_base = tiles;
         fc.slot_base = NLIST * tiles;
-        fc.rec_base = (long long)v * c->n;
+        fc.rec_base = (long long)v * src_n(c);
         if ((int64_t)tiles + fc.ntiles > (int64_t)0x7FFFFFFF / (2 * NLIST)) return SPL_EINVAL;
         tiles += fc.ntiles;
         c->h_fcs[v] = fc;
         c->h_images[v] = images[v];
     }
-    if ((int64_t)V * c->n > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // record ids are 32-bit
-    const size_t recs = (size_t)V * (size_t)c->n;
+    if ((int64_t)V * src_n(c) > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // record ids are 32-bit
+    const size_t recs = (size_t)V * (size_t)src_n(c);
     SPL_TRY(grow(c, c->rec0, recs ? recs : 1));
     SPL_TRY(grow(c, c->rec1, recs ? recs : 1));
     SPL_TRY(grow(c, c->large_ids, recs ? recs : 1));
@@ -478,7 +502,7 @@ static int prepare_views(spl_ctx *c, const spl_camera *cams, int V, float *const
     vs.nviews = V;
     vs.total_tiles = tiles;
     vs.tile = c->par.tile_px;
-    vs.n = c->n;
+    vs.n = src_n(c);
     return SPL_OK;
 }
 
@@ -501,15 +525,21 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
     cudaMemsetAsync(c->counts.p, 0, sizeof(int) * NLIST * vs.total_tiles, s);
     cudaMemsetAsync(c->dstats.p, 0, offsetof(DevStats, err), s);
     RasterArgs ra{};
-    ra.n = c->n;
-    ra.x = c->x.p; ra.y = c->y.p; ra.z = c->z.p;
-    ra.h = c->h.p; ra.I = c->I.p; ra.s = c->s.p;
+    ra.n = src_n(c);
+    if (c->streaming) {
+        const int b = c->chunk_buf;
+        ra.x = c->cx[b].p; ra.y = c->cy[b].p; ra.z = c->cz[b].p;
+        ra.h = c->ch[b].p; ra.I = c->cI[b].p; ra.s = c->cs[b].p;
+    } else {
+        ra.x = c->x.p; ra.y = c->y.p; ra.z = c->z.p;
+        ra.h = c->h.p; ra.I = c->I.p; ra.s = c->s.p;
+    }
     ra.pal = c->pal.p;
     ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
     ra.counts = c->counts.p;
     ra.large_ids = c->large_ids.p;
     ra.st = c->dstats.p;
-    launch_raster(vs, ra, c->attr_type, s);
+    launch_raster(vs, ra, c->streaming ? c->chunk_attr : c->attr_type, s);
     record_event(c, 1, s);
     BinArgs ba{};
     ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
@@ -527,7 +557,7 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
 
 // Stage 2: clear the images, fill the tile lists and work items, render.
 static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStream_t s) {
-    launch_zero_images(vs, c->d_images.p, c->sms, s);
+    if (!c->accumulate) launch_zero_images(vs, c->d_images.p, c->sms, s);
     BinArgs ba{};
     ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
     ba.large_ids = c->large_ids.p;
@@ -547,6 +577,7 @@ static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
     ta.items_cap = (int)c->items.cap;
     ta.images = c->d_images.p;
     ta.st = c->dstats.p;
+    ta.accumulate = c->accumulate ? 1 : 0;
     // scheduling: per-item features, predicted cost, longest first
     const bool sched = c->par.sched != SPL_SCHED_NONE;
     // exact features when recording training samples, else a 64-entry sample
@@ -566,7 +597,7 @@ static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
     record_event(c, 3, s);
     if (large_pass) launch_large_pass(vs, ta, c->sms, s);
     record_event(c, 4, s);
-    if (c->par.mode == SPL_MODE_EA) launch_epilogue_views(vs, c->d_images.p, c->sms, s);
+    if (c->par.mode == SPL_MODE_EA && c->last_chunk) launch_epilogue_views(vs, c->d_images.p, c->sms, s);
     record_event(c, 5, s);
 }
 
@@ -574,7 +605,7 @@ static void fill_stats(spl_ctx *c, const Views &vs, int launches) {
     spl_stats &st = c->last;
     std::memset(&st, 0, sizeof(st));
     st.launches = launches;
-    st.n_particles = c->n;
+    st.n_particles = src_n(c);
     st.n_active = (int64_t)c->hstats->n_active;
     st.n_point = (int64_t)c->hstats->n_point;
     st.n_small = (int64_t)c->hstats->n_small;
@@ -589,7 +620,7 @@ static void fill_stats(spl_ctx *c, const Views &vs, int launches) {
 // exactly, then the passes.
 static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const *images,
                         cudaStream_t s) {
-    if (!c->have_particles || c->npal < 1) return SPL_ESTATE;
+    if ((!c->have_particles && !c->streaming) || c->npal < 1) return SPL_ESTATE;
     Views vs{};
     SPL_TRY(prepare_views(c, cams, V, images, vs));
     SPL_CUDA(cudaGetLastError());
@@ -613,8 +644,9 @@ static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const 
     c->last_items = n_tile_items + n_large_items;
     enqueue_render(c, vs, n_large_items > 0, s);
     SPL_CUDA(cudaGetLastError());
-    const int launches = 5 + (c->n > 0 ? 4 : 0) + 1 + (n_large_items > 0 ? 1 : 0) +
-                         (c->par.mode == SPL_MODE_EA ? 1 : 0) +
+    const int launches = 4 + (c->accumulate ? 0 : 1) + (src_n(c) > 0 ? 4 : 0) + 1 +
+                         (n_large_items > 0 ? 1 : 0) +
+                         (c->par.mode == SPL_MODE_EA && c->last_chunk ? 1 : 0) +
                          (c->par.sched != SPL_SCHED_NONE || c->recording ? 1 : 0) +
                          (c->par.sched != SPL_SCHED_NONE ? 4 : 0);
     if (c->timing) {
@@ -650,6 +682,109 @@ extern "C" int spl_render_host(spl_ctx *c, float *h_image) {
 // Configuration a captured batch graph is valid for: everything that shapes
 // the launches or the buffer sizes (cameras themselves may change: their
 // constants are copied from the pinned staging at replay time).
+// Out-of-core render (Sec. 3.2, Eq. 3): the particles stay in host memory
+// and pass through the device in chunks; chunk k+1 is copied on the copy
+// stream while chunk k's tile lists are filled and rendered on the render
+// stream (two device buffers, events in both directions), and every chunk
+// adds its additive image into d_image (the sum is linear in the particle
+// set, Sec. 2); the E=A map, if selected, follows the last chunk.
+static int copy_chunk(spl_ctx *c, const spl_particles *p, int64_t first, int64_t cnt, int b) {
+    const size_t ah = p->attr_type == SPL_ATTR_F16 ? 2 : 4;
+    const size_t ab = p->attr_type == SPL_ATTR_F32 ? 4 : 2;
+    const size_t m = (size_t)cnt;
+    cudaStream_t cs = c->copy_stream;
+    SPL_CUDA(cudaStreamWaitEvent(cs, c->consumed[b], 0));
+    SPL_CUDA(cudaMemcpyAsync(c->cx[b].p, p->x + first, m * 4, cudaMemcpyHostToDevice, cs));
+    SPL_CUDA(cudaMemcpyAsync(c->cy[b].p, p->y + first, m * 4, cudaMemcpyHostToDevice, cs));
+    SPL_CUDA(cudaMemcpyAsync(c->cz[b].p, p->z + first, m * 4, cudaMemcpyHostToDevice, cs));
+    SPL_CUDA(cudaMemcpyAsync(c->ch[b].p, (const unsigned char *)p->h + first * ah, m * ah,
+                             cudaMemcpyHostToDevice, cs));
+    SPL_CUDA(cudaMemcpyAsync(c->cI[b].p, (const unsigned char *)p->I + first * ab, m * ab,
+                             cudaMemcpyHostToDevice, cs));
+    SPL_CUDA(cudaMemcpyAsync(c->cs[b].p, (const unsigned char *)p->s + first * ab, m * ab,
+                             cudaMemcpyHostToDevice, cs));
+    SPL_CUDA(cudaEventRecord(c->copied[b], cs));
+    return SPL_OK;
+}
+
+extern "C" int spl_render_stream(spl_ctx *c, const spl_particles *p, int64_t chunk, float *d_image,
+                                 void *stream) {
+    if (!c || !p || !d_image || chunk < 1 || p->n < 0) return SPL_EINVAL;
+    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
+    if (p->mem_space != SPL_MEM_HOST) return SPL_EINVAL;
+    if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
+    if (!c->have_cam) return SPL_ESTATE;
+    if (c->npal < 1) return SPL_ESTATE;
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    if (!c->copy_stream) {
+        SPL_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            SPL_CUDA(cudaEventCreateWithFlags(&c->copied[b], cudaEventDisableTiming));
+            SPL_CUDA(cudaEventCreateWithFlags(&c->consumed[b], cudaEventDisableTiming));
+        }
+    }
+    const int64_t per = p->n < chunk ? (p->n > 0 ? p->n : 1) : chunk;
+    const size_t ah = p->attr_type == SPL_ATTR_F16 ? 2 : 4;
+    const size_t ab = p->attr_type == SPL_ATTR_F32 ? 4 : 2;
+    for (int b = 0; b < 2; ++b) {
+        SPL_TRY(c->cx[b].ensure((size_t)per));
+        SPL_TRY(c->cy[b].ensure((size_t)per));
+        SPL_TRY(c->cz[b].ensure((size_t)per));
+        SPL_TRY(c->ch[b].ensure((size_t)per * ah));
+        SPL_TRY(c->cI[b].ensure((size_t)per * ab));
+        SPL_TRY(c->cs[b].ensure((size_t)per * ab));
+        SPL_CUDA(cudaEventRecord(c->consumed[b], s));   // the buffers are free from here on
+    }
+    const int64_t nchunks = p->n > 0 ? (p->n + chunk - 1) / chunk : 1;
+    int64_t tot[5] = {}, ents[4] = {};
+    int rc = SPL_OK;
+    if (p->n > 0) rc = copy_chunk(c, p, 0, per < p->n ? per : p->n, 0);
+    c->streaming = true;
+    c->chunk_attr = p->attr_type;
+    for (int64_t k = 0; k < nchunks && rc == SPL_OK; ++k) {
+        const int b = (int)(k & 1);
+        const int64_t first = k * chunk;
+        const int64_t cnt = p->n > 0 ? (p->n - first < chunk ? p->n - first : chunk) : 0;
+        if (cnt > 0) {
+            rc = cuda_status(cudaStreamWaitEvent(s, c->copied[b], 0));
+            if (rc != SPL_OK) break;
+        }
+        c->chunk_buf = b;
+        c->chunk_n = cnt;
+        c->accumulate = k > 0;
+        c->last_chunk = k + 1 == nchunks;
+        rc = render_views(c, &c->cam, 1, &d_image, s);
+        if (rc != SPL_OK) break;
+        rc = cuda_status(cudaEventRecord(c->consumed[b], s));
+        // the next chunk's copy starts once this chunk's binning is done (render_views
+        // has synchronised after it), so that it overlaps the scatter and tile pass
+        // and does not queue the small per-chunk uploads behind a large copy
+        if (rc == SPL_OK && k + 1 < nchunks) {
+            const int64_t nf = first + chunk;
+            rc = copy_chunk(c, p, nf, p->n - nf < chunk ? p->n - nf : chunk, b ^ 1);
+        }
+        const spl_stats &st = c->last;
+        tot[0] += st.n_active; tot[1] += st.n_point; tot[2] += st.n_small;
+        tot[3] += st.n_medium; tot[4] += st.n_large;
+        for (int l = 0; l < 4; ++l) ents[l] += st.n_entries[l];
+    }
+    c->streaming = false;
+    c->accumulate = false;
+    c->last_chunk = true;
+    // the copy stream must not outlive the caller's host buffers
+    const int rc2 = cuda_status(cudaStreamSynchronize(c->copy_stream));
+    if (rc != SPL_OK) return rc;
+    c->last.n_particles = p->n;
+    c->last.n_active = tot[0];
+    c->last.n_point = tot[1];
+    c->last.n_small = tot[2];
+    c->last.n_medium = tot[3];
+    c->last.n_large = tot[4];
+    for (int l = 0; l < 4; ++l) c->last.n_entries[l] = ents[l];
+    return rc2;
+}
+
 static unsigned long long batch_key(const spl_ctx *c, const spl_camera *cams, int V) {
     unsigned long long h = 1469598103934665603ULL;
     auto mix = [&h](const void *p, size_t n) {

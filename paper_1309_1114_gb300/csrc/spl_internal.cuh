@@ -128,6 +128,7 @@ struct TileArgs {
     DevStats *st;
     const int *order;          // optional: processing order of each pass's items
     long long *item_cycles;    // optional: SM clock cycles spent on each item
+    int accumulate;            // add into the images instead of storing (streamed chunks)
 };
 
 // Tile-cost network 32 -> 64 (ReLU) -> 1; parameter vector layout

@@ -427,7 +427,8 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
             __syncthreads();
         }
 
-        // write: shared part + registers, stored (only item of its tile) or added
+        // write: shared part + registers, stored (only item of its tile; added
+        // to the previous chunks' sum when accumulating) or added atomically
         const bool store = !LARGE && list < 0;
         float *image = a.images[view];
 #pragma unroll
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
                 for (int c = 0; c < 3; ++c) {
                     const float v = sacc[c][row][cx] + acc.get(q, k, c);
                     if (store)
-                        dst[c] = v;
+                        dst[c] = a.accumulate ? dst[c] + v : v;
                     else if (v != 0.f)
                         atomicAdd(dst + c, v);
                 }

@@ -70,6 +70,7 @@ _SIGS = {
     "spl_get_params": [_P, C.POINTER(spl_params)],
     "spl_render": [_P, _P, _P],
     "spl_render_host": [_P, _P],
+    "spl_render_stream": [_P, C.POINTER(spl_particles), C.c_int64, _P, _P],
     "spl_render_batch": [_P, C.POINTER(spl_camera), C.c_int32, C.POINTER(C.c_void_p), _P],
     "spl_get_stats": [_P, C.POINTER(spl_stats)],
     "spl_set_timing": [_P, C.c_int32],
@@ -194,9 +195,11 @@ class Renderer:
     def handle(self):
         return self._h
 
-    def load(self, parts: dict, fp16: dict | None = None):
-        """Load particles.  fp16 (optional) holds binary16 arrays that replace
-        parts' h, I and s (SPL_ATTR_F16), or only I and s (SPL_ATTR_F16_IS)."""
+    @staticmethod
+    def _particles(parts: dict, fp16: dict | None):
+        """spl_particles for parts (and the arrays it points to, kept alive by
+        the caller).  fp16 (optional) holds binary16 arrays that replace parts'
+        h, I and s (SPL_ATTR_F16), or only I and s (SPL_ATTR_F16_IS)."""
         src = dict(parts)
         attr = SPL_ATTR_F32
         if fp16 is not None:
@@ -217,7 +220,23 @@ class Renderer:
                     raise ValueError("particle arrays: wrong dtype or shape")
         p = spl_particles(n, *[_ptr(a) for a in arrs], attr,
                           SPL_MEM_DEVICE if any(on_dev) else SPL_MEM_HOST)
+        return p, arrs
+
+    def load(self, parts: dict, fp16: dict | None = None):
+        """Load particles (host or device arrays; see _particles for fp16)."""
+        p, keep = self._particles(parts, fp16)
         check(load_library().spl_load_particles(self._h, C.byref(p)), "spl_load_particles")
+        del keep
+
+    def render_stream(self, parts: dict, chunk: int, image, fp16: dict | None = None,
+                      stream: int | None = None):
+        """Out-of-core render of host particle arrays (page-locked for overlap)
+        in chunks of `chunk` particles into the device image."""
+        p, keep = self._particles(parts, fp16)
+        check(load_library().spl_render_stream(self._h, C.byref(p), int(chunk), image.data_ptr(),
+                                               stream), "spl_render_stream")
+        del keep
+        return image
 
     def set_camera(self, cam: dict):
         c = make_camera(cam)
