@@ -16,6 +16,11 @@ the header comment of ``splotch_oracle.c``.  Parity status per function:
   ``tests/test_oracle_mlp.py``.
 * ``tile_features``: pinned by hand-counted cases in
   ``tests/test_oracle_pins.py``.
+* ``render`` / ``render_bruteforce`` with ``mode = 2`` (Eq. 1 with independent
+  emission and absorption over depth-ordered particles): pinned by hand-worked
+  two-particle cases (both orders, equal depths), the E = A special case, the
+  optically thin and opaque limits, input-order invariance and the pixel-major
+  brute force in ``tests/test_oracle_absorb.py``.
 """
 from __future__ import annotations
 
@@ -43,7 +48,7 @@ class _Params(C.Structure):
     _fields_ = [("chi", C.c_double), ("sigma_per_h", C.c_double),
                 ("s_box", C.c_double), ("r_sml", C.c_double),
                 ("brightness", C.c_double), ("s_min", C.c_double),
-                ("s_max", C.c_double), ("mode", C.c_int)]
+                ("s_max", C.c_double), ("mode", C.c_int), ("absorption", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -112,6 +117,7 @@ def _params(par: dict | None) -> _Params:
     q.s_min = float(par.get("s_min", 0.0))
     q.s_max = float(par.get("s_max", 1.0))
     q.mode = int(par.get("mode", 0))
+    q.absorption = float(par.get("absorption", 1.0))
     return q
 
 

@@ -26,6 +26,11 @@
  *   Sec. 4 classification: particles with r <= r_sml (= 0.5) fall inside a
  *     single pixel; only their location is computed, and the oracle deposits
  *     their emission once into that pixel.
+ *   Eq. 1 in general (E_p != A_p, mode 2): the particles a ray crosses are
+ *     taken one after the other from the far end towards the observer, and
+ *     across particle p the solution of Eq. 1 is
+ *     I -> I exp(-tau_p) + (E_p / A_p)(1 - exp(-tau_p)), tau_p = A_p w_p
+ *     (see orc_render_absorb for the reading of E_p, A_p and the order).
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - sigma_p = sigma_per_h * h (default 1: sigma_p is the smoothing length);
@@ -64,7 +69,8 @@ typedef struct {
     double r_sml;        /* point-rule radius of Sec. 4 (0.5) */
     double brightness;   /* global emission scale */
     double s_min, s_max; /* colour-scalar normalisation (Sec. 4 footnote) */
-    int mode;            /* 0: additive sum, 1: E=A map 1-exp(-S) */
+    int mode;            /* 0: additive sum, 1: E=A map 1-exp(-S), 2: absorption */
+    double absorption;   /* mode 2: A_p = absorption * brightness * I_p (> 0) */
 } orc_params;
 
 /* Class labels written by orc_project. */
@@ -122,6 +128,8 @@ static int make_view(const orc_camera *c, orc_view *v) {
 typedef struct {
     double xs, ys, sigma, r;
     double e[3];
+    double zc;           /* camera depth */
+    double ib;           /* brightness * intensity */
     int cls;
 } orc_rec;
 
@@ -156,6 +164,8 @@ static void project_one(const orc_view *v, const orc_params *q, const float *pal
     o->cls = ORC_INACTIVE;
     o->xs = o->ys = o->sigma = o->r = 0.0;
     o->e[0] = o->e[1] = o->e[2] = 0.0;
+    o->zc = zc;
+    o->ib = q->brightness * inten;
     if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(hh) || !isfinite(inten) ||
         !isfinite(sc) || hh < 0.0)
         return;
@@ -244,12 +254,18 @@ int orc_project(long n, const float *x, const float *y, const float *z,
 /* Full image, particle-major.  nthreads > 1 gives each OpenMP thread its own
  * partial image over a contiguous chunk of particles and sums the partial
  * images afterwards (the MPI/OpenMP scheme of Sec. 2). */
+static int render_absorb(long n, const float *x, const float *y, const float *z,
+                         const float *h, const float *inten, const float *s,
+                         const float *pal, int npal, const orc_view *v,
+                         const orc_params *q, double *img, int pixel_major);
+
 int orc_render(long n, const float *x, const float *y, const float *z,
                const float *h, const float *inten, const float *s,
                const float *pal, int npal, const orc_camera *cam,
                const orc_params *q, double *img, int nthreads) {
     orc_view v;
     if (npal < 1 || make_view(cam, &v)) return -1;
+    if (q->mode == 2) return render_absorb(n, x, y, z, h, inten, s, pal, npal, &v, q, img, 0);
     long npx = (long)v.w * v.h;
     memset(img, 0, sizeof(double) * 3 * npx);
     if (nthreads < 1) nthreads = 1;
@@ -380,6 +396,7 @@ int orc_render_bruteforce(long n, const float *x, const float *y, const float *z
                           const orc_params *q, double *img) {
     orc_view v;
     if (npal < 1 || make_view(cam, &v)) return -1;
+    if (q->mode == 2) return render_absorb(n, x, y, z, h, inten, s, pal, npal, &v, q, img, 1);
     orc_rec *rec = (orc_rec *)malloc(sizeof(orc_rec) * (n > 0 ? n : 1));
     if (!rec) return -2;
     for (long p = 0; p < n; ++p)
@@ -392,6 +409,132 @@ int orc_render_bruteforce(long n, const float *x, const float *y, const float *z
         }
     free(rec);
     finish(q, img, (long)v.w * v.h);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Eq. 1 with independent emission and absorption (mode 2)                 */
+/* ---------------------------------------------------------------------- */
+/*
+ * Along the line of sight of a pixel the particles are crossed one after the
+ * other.  Across particle p Eq. 1 has the solution
+ *     I -> I exp(-tau_p) + (E_p / A_p) (1 - exp(-tau_p)),   tau_p = A_p w_p,
+ * where w_p is the particle's clipped Gaussian weight of Eq. 2 at the pixel
+ * (weight 1 at its pixel for a point particle), the line-integral factor being
+ * folded into rho0 as in the additive form.  Readings (the paper gives no
+ * formula for the coefficients):
+ *   - emission E_p (RGB) is the additive form's emission, brightness * I_p *
+ *     colour(s_p); absorption is grey, A_p = absorption * brightness * I_p
+ *     (absorption > 0), so the source term E_p / A_p = colour(s_p) /
+ *     absorption varies between particles and the order matters;
+ *   - a particle with A_p = 0 (I_p = 0) emits nothing and absorbs nothing;
+ *   - the ray starts with I = 0 behind the farthest particle and ends at the
+ *     observer: particles are taken in decreasing camera depth, the depth key
+ *     being z_c rounded to float, equal keys in decreasing particle index (so
+ *     that the ascending (key, index) order runs front to back);
+ *   - with a constant palette equal to `absorption` in every channel E_p = A_p,
+ *     and the result is the E=A map 1 - exp(-S) of mode 1.
+ * pixel_major = 0: particle-major over the sorted particles, an H*W*3 image
+ * updated in place; pixel_major = 1: every pixel sorts its own contributing
+ * particles (the brute force of the tests).
+ */
+typedef struct {
+    float key;
+    long id;
+} orc_depth;
+
+static int cmp_back_to_front(const void *pa, const void *pb) {
+    const orc_depth *a = (const orc_depth *)pa, *b = (const orc_depth *)pb;
+    if (a->key != b->key) return a->key > b->key ? -1 : 1;
+    if (a->id != b->id) return a->id > b->id ? -1 : 1;
+    return 0;
+}
+
+/* Crossing of one particle with weight w by the ray of pixel value I[3]. */
+static void cross_particle(const orc_rec *o, const orc_params *q, double w, double *I) {
+    double A = q->absorption * o->ib;
+    double tau = A * w;
+    double keep = exp(-tau), gain = -expm1(-tau);
+    for (int k = 0; k < 3; ++k) I[k] = I[k] * keep + (o->e[k] / A) * gain;
+}
+
+/* Weight of particle o at pixel (i, j): Eq. 2 clipped, or the point rule;
+ * returns 0 where the particle does not reach the pixel. */
+static double pixel_weight(const orc_rec *o, long i, long j) {
+    if (o->cls == ORC_POINT)
+        return floor(o->xs) == (double)i && floor(o->ys) == (double)j ? 1.0 : 0.0;
+    if (o->cls != ORC_SPLAT) return 0.0;
+    double dx = (i + 0.5) - o->xs, dy = (j + 0.5) - o->ys;
+    double d2 = dx * dx + dy * dy;
+    return d2 <= o->r * o->r ? exp(-d2 / (o->sigma * o->sigma)) : 0.0;
+}
+
+static int render_absorb(long n, const float *x, const float *y, const float *z,
+                         const float *h, const float *inten, const float *s,
+                         const float *pal, int npal, const orc_view *v,
+                         const orc_params *q, double *img, int pixel_major) {
+    if (!(q->absorption > 0.0)) return -1;
+    long npx = (long)v->w * v->h;
+    memset(img, 0, sizeof(double) * 3 * npx);
+    orc_rec *rec = (orc_rec *)malloc(sizeof(orc_rec) * (n > 0 ? n : 1));
+    orc_depth *ord = (orc_depth *)malloc(sizeof(orc_depth) * (n > 0 ? n : 1));
+    if (!rec || !ord) {
+        free(rec);
+        free(ord);
+        return -2;
+    }
+    long m = 0;
+    for (long p = 0; p < n; ++p) {
+        project_one(v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p], s[p], &rec[p]);
+        if (rec[p].cls != ORC_INACTIVE && q->absorption * rec[p].ib != 0.0) {
+            ord[m].key = (float)rec[p].zc;
+            ord[m].id = p;
+            ++m;
+        }
+    }
+    if (!pixel_major) {
+        qsort(ord, (size_t)m, sizeof(orc_depth), cmp_back_to_front);
+        for (long k = 0; k < m; ++k) {
+            const orc_rec *o = &rec[ord[k].id];
+            double i0, i1, j0, j1;
+            if (o->cls == ORC_POINT) {
+                i0 = i1 = floor(o->xs);
+                j0 = j1 = floor(o->ys);
+            } else {
+                i0 = ceil(o->xs - o->r - 0.5); i1 = floor(o->xs + o->r - 0.5);
+                j0 = ceil(o->ys - o->r - 0.5); j1 = floor(o->ys + o->r - 0.5);
+            }
+            if (i0 < 0.0) i0 = 0.0;
+            if (j0 < 0.0) j0 = 0.0;
+            if (i1 > v->w - 1) i1 = v->w - 1;
+            if (j1 > v->h - 1) j1 = v->h - 1;
+            for (long j = (long)j0; j <= (long)j1; ++j)
+                for (long i = (long)i0; i <= (long)i1; ++i) {
+                    double w = pixel_weight(o, i, j);
+                    if (w > 0.0) cross_particle(o, q, w, img + 3 * (j * v->w + i));
+                }
+        }
+    } else {
+        orc_depth *hit = (orc_depth *)malloc(sizeof(orc_depth) * (m > 0 ? m : 1));
+        if (!hit) {
+            free(rec);
+            free(ord);
+            return -2;
+        }
+        for (long j = 0; j < v->h; ++j)
+            for (long i = 0; i < v->w; ++i) {
+                long c = 0;
+                for (long k = 0; k < m; ++k)
+                    if (pixel_weight(&rec[ord[k].id], i, j) > 0.0) hit[c++] = ord[k];
+                qsort(hit, (size_t)c, sizeof(orc_depth), cmp_back_to_front);
+                double *I = img + 3 * (j * v->w + i);
+                for (long k = 0; k < c; ++k)
+                    cross_particle(&rec[hit[k].id], q, pixel_weight(&rec[hit[k].id], i, j), I);
+            }
+        free(hit);
+    }
+    free(rec);
+    free(ord);
     return 0;
 }
 
@@ -456,11 +599,18 @@ int orc_ambiguity(long n, const float *x, const float *y, const float *z,
     orc_view v;
     if (npal < 1 || make_view(cam, &v)) return -1;
     memset(B, 0, sizeof(double) * 3 * (long)v.w * v.h);
+    /* mode 2: a contribution tau = A w that flips changes the pixel by at most
+     * tau * max(E/A) = brightness * I * w * (largest palette value) in every
+     * channel (the pixel value stays between 0 and the largest source term) */
+    double pal_max = 0.0;
+    for (long k = 0; k < 3L * npal; ++k) pal_max = fmax(pal_max, fabs((double)pal[k]));
     long cnt = 0;
     for (long p = 0; p < n; ++p) {
         orc_rec o;
         project_one(&v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
         if (o.cls == ORC_INACTIVE) continue;
+        if (q->mode == 2)
+            for (int k = 0; k < 3; ++k) o.e[k] = fabs(o.ib) * pal_max;
         int class_amb = fabs(o.r - q->r_sml) < 1e-6 * q->r_sml;
         int pix_amb = (o.cls == ORC_POINT) &&
                       (fabs(o.xs - floor(o.xs + 0.5)) < 1e-5 ||
