@@ -43,6 +43,11 @@ WORKLOADS = {
                         "desc": "100M clustered particles, I/s stored FP16, h FP32, 2048x2048 RGB FP32"},
     "precision32": {"scene": "precision", "label": "clustered-100M-2048sq-f32",
                     "desc": "100M clustered particles, FP32 attributes, 2048x2048 RGB FP32"},
+    "absorb": {"scene": "clustered", "label": "clustered-10M-1024sq-f32-absorb",
+               "params": {"mode": 2, "absorption": 1.0},
+               "desc": "the clustered 10M / 1024x1024 workload rendered with Eq. 1's general "
+                       "absorption (grey absorption A = I, coloured emission): tile lists "
+                       "radix-sorted by depth, front-to-back compositing"},
     "uniform": {"scene": "uniform", "label": "uniform-200k-256sq-f32",
                 "desc": "200k uniform particles, log-normal h, 256x256 RGB FP32"},
     "pareto": {"scene": "pareto", "label": "pareto-400M-4096sq-f32", "sched": True,
@@ -59,6 +64,9 @@ WORKLOADS = {
 METRIC = "particles/s per GB300 at stated error vs FP64 oracle; % of HBM roofline"
 FLOPS_PER_PAIR = 7      # separable weight product (1 mul) + 3 multiply-adds
 FLOPS_PER_POINT = 3     # 3 adds
+# absorption: tau (2 mul), 1 - exp(-tau) (1 transcendental + 1), T (1 - e^-tau)
+# (1 mul), 3 multiply-adds into C, the transmittance update (1)
+FLOPS_PER_ABSORB = 11
 FP32_LANES_PER_SM = 128
 
 
@@ -162,18 +170,24 @@ def profiled_traffic(kernel: str, label: str):
     return e.get("dram_bytes_per_launch")
 
 
-def oracle_sample_rate(scene, cam, target_s: float, seed: int = 0):
-    """Time the FP64 oracle (all host cores) on a random sample of the scene,
-    sized to take about target_s seconds.  Returns (particles/s, sample, cores, secs)."""
+def oracle_par(wl: dict) -> dict:
+    return {k: v for k, v in wl.get("params", {}).items() if k in ("mode", "absorption")}
+
+
+def oracle_sample_rate(scene, cam, target_s: float, seed: int = 0, par=None):
+    """Time the FP64 oracle (all host cores; one for the depth-ordered absorption
+    mode, which the oracle runs serially) on a random sample of the scene, sized
+    to take about target_s seconds.  Returns (particles/s, sample, cores, secs)."""
     import oracle
-    cores = os.cpu_count() or 1
+    par = dict(par or {})
+    cores = 1 if par.get("mode") == 2 else (os.cpu_count() or 1)
     rng = np.random.default_rng(seed)
     m = min(scene.n, 20000)
     for _ in range(4):
         idx = np.sort(rng.choice(scene.n, m, replace=False))
         sub = {k: v[idx] for k, v in scene.parts.items()}
         t0 = time.perf_counter()
-        oracle.render(sub, scene.palette, cam, {}, nthreads=cores)
+        oracle.render(sub, scene.palette, cam, par, nthreads=cores)
         dt = time.perf_counter() - t0
         if dt >= 0.5 * target_s or m == scene.n:
             return m / dt, m, cores, dt
@@ -193,7 +207,7 @@ def run_reference(args, wl):
     scene = make_scene(wl)
     cam = scene.cams[0]
     # size one step to ~2 s of oracle work on all cores
-    rate, m, cores, _ = oracle_sample_rate(scene, cam, 2.0)
+    rate, m, cores, _ = oracle_sample_rate(scene, cam, 2.0, par=oracle_par(wl))
     import oracle
     rng = np.random.default_rng(1)
     times = []
@@ -201,7 +215,7 @@ def run_reference(args, wl):
         idx = np.sort(rng.choice(scene.n, m, replace=False))
         sub = {kk: v[idx] for kk, v in scene.parts.items()}
         t0 = time.perf_counter()
-        oracle.render(sub, scene.palette, cam, {}, nthreads=cores)
+        oracle.render(sub, scene.palette, cam, oracle_par(wl), nthreads=cores)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
@@ -403,7 +417,7 @@ def run_ours(args, wl):
     r.load(scene.parts, fp16)
     r.set_colormap(scene.palette)
     r.set_camera(cam)
-    r.set_params()
+    r.set_params(**wl.get("params", {}))
     sched_mode = 0
     model_info = None
     if wl.get("sched"):
@@ -415,7 +429,7 @@ def run_ours(args, wl):
             sched_mode = 2
             with open(train_scheduler.DEFAULT_OUT) as fh:
                 model_info = {k: v for k, v in json.load(fh).items() if k not in ("theta", "heur")}
-        r.set_params(sched=sched_mode)
+        r.set_params(sched=sched_mode, **wl.get("params", {}))
     img = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
     work = r.count_work()
 
@@ -454,12 +468,16 @@ def run_ours(args, wl):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12    # TFLOP/s
-    tile_flops = FLOPS_PER_POINT * work[0] + FLOPS_PER_PAIR * (work[1] + work[2])
-    large_flops = FLOPS_PER_PAIR * work[3]
+    absorbing = wl.get("params", {}).get("mode") == 2
+    per_pair = FLOPS_PER_ABSORB if absorbing else FLOPS_PER_PAIR
+    per_point = FLOPS_PER_ABSORB if absorbing else FLOPS_PER_POINT
+    tile_flops = per_point * work[0] + per_pair * (work[1] + work[2])
+    large_flops = per_pair * work[3]
     dom = "tile" if stage["tile"] >= stage["large"] else "large"
     flops = tile_flops if dom == "tile" else large_flops
     achieved = flops / (stage[dom] * 1e-3) / 1e12 if stage[dom] > 0 else 0.0
-    kname = f"item_kernel<{st['tile_px']}, {0 if dom == 'tile' else 1}>"
+    kname = (f"absorb_kernel<{st['tile_px']}>" if absorbing else
+             f"item_kernel<{st['tile_px']}, {0 if dom == 'tile' else 1}>")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
                 "kernel": kname, "kernel_ms": stage[dom],
@@ -467,7 +485,7 @@ def run_ours(args, wl):
                               f"{sm_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
                 "work": {"point_deposits": work[0], "small_pairs": work[1],
                          "medium_pairs": work[2], "large_pairs": work[3],
-                         "flops_per_pair": FLOPS_PER_PAIR}}
+                         "flops_per_pair": per_pair}}
     schedulers = None
     if wl.get("sched"):
         # the same frame with each scheduler (CUDA-event frame times, 5 frames each)
@@ -520,7 +538,7 @@ def run_ours(args, wl):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, m, cores, secs = oracle_sample_rate(scene, cam, 10.0)
+        rate, m, cores, secs = oracle_sample_rate(scene, cam, 10.0, par=oracle_par(wl))
         cpu = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
                "sample": f"{m} particles drawn at random from the workload, full {W}x{H} image, "
                          f"FP64, OpenMP over {cores} threads, {secs:.1f} s"}

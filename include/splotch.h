@@ -65,6 +65,13 @@ extern "C" {
 /* output modes */
 #define SPL_MODE_ADDITIVE 0   /* image = sum of clipped Gaussians (Eq. 1, E_p = A_p, thin) */
 #define SPL_MODE_EA 1         /* image = 1 - exp(-sum), the E_p = A_p solution of Eq. 1 */
+#define SPL_MODE_ABSORB 2     /* Eq. 1 with E_p != A_p over depth-ordered particles: emission
+                               * E_p = brightness I_p colour(s_p), grey absorption
+                               * A_p = absorption * brightness * I_p; across particle p a ray
+                               * becomes I exp(-tau) + (E_p/A_p)(1 - exp(-tau)), tau = A_p w_p,
+                               * particles crossed from the farthest to the nearest (depth key
+                               * z_c in FP32, ties by particle index); single views only
+                               * (spl_render, spl_render_host) */
 
 /* tile schedulers */
 #define SPL_SCHED_NONE 0      /* tiles in image order */
@@ -111,8 +118,9 @@ typedef struct {
     double r_small;            /* r_sml < r <= r_small: one warp per particle over its pixel box
                                 * (default 0.5 = r_sml: no such class, the tile pass takes them) */
     double r_large;            /* r > r_large: large pass (default 64) */
-    int32_t mode;              /* SPL_MODE_ADDITIVE or SPL_MODE_EA */
+    int32_t mode;              /* SPL_MODE_ADDITIVE, SPL_MODE_EA or SPL_MODE_ABSORB */
     int32_t sched;             /* SPL_SCHED_* (default SPL_SCHED_NONE) */
+    double absorption;         /* SPL_MODE_ABSORB: A_p = absorption * brightness * I_p, > 0 (default 1) */
 } spl_params;
 
 /* Per-frame statistics of the last render (counts are exact).  With timing

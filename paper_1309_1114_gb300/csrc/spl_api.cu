@@ -83,6 +83,13 @@ struct spl_ctx {
     spl_params par{};
     // scratch
     DevBuf<float4> rec0, rec1;
+    // absorption mode: (A, depth key) per record, the depth-order sort, and the
+    // (C, T) partials of split tiles
+    DevBuf<float2> rec2;
+    DevBuf<unsigned long long> pkeys, ptmp, ekeys, etmp;
+    DevBuf<unsigned> rank;
+    DevBuf<int> sort_hist;
+    DevBuf<float4> partial;
     DevBuf<int> counts;
     DevBuf<long long> offsets, cursor;
     DevBuf<unsigned> large_ids, entries;
@@ -161,6 +168,7 @@ extern "C" int spl_default_params(spl_params *q) {
     q->r_large = 64.0;
     q->mode = SPL_MODE_ADDITIVE;
     q->sched = SPL_SCHED_NONE;
+    q->absorption = 1.0;
     return SPL_OK;
 }
 
@@ -170,8 +178,9 @@ static bool params_ok(const spl_params *q) {
            std::isfinite(q->r_sml) && q->r_sml >= 0 && std::isfinite(q->brightness) &&
            (q->tile_px == 16 || q->tile_px == 32 || q->tile_px == 64) && std::isfinite(q->r_small) &&
            q->r_small >= q->r_sml && std::isfinite(q->r_large) && q->r_large >= q->r_small &&
-           (q->mode == SPL_MODE_ADDITIVE || q->mode == SPL_MODE_EA) && q->sched >= 0 &&
-           q->sched <= SPL_SCHED_MLP;
+           (q->mode == SPL_MODE_ADDITIVE || q->mode == SPL_MODE_EA || q->mode == SPL_MODE_ABSORB) &&
+           q->sched >= 0 && q->sched <= SPL_SCHED_MLP && std::isfinite(q->absorption) &&
+           q->absorption > 0;
 }
 
 static bool camera_ok(const spl_camera *c) {
@@ -250,6 +259,8 @@ extern "C" int spl_destroy(spl_ctx *c) {
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     c->pal.release();
     c->rec0.release(); c->rec1.release();
+    c->rec2.release(); c->pkeys.release(); c->ptmp.release(); c->ekeys.release();
+    c->etmp.release(); c->rank.release(); c->sort_hist.release(); c->partial.release();
     c->counts.release(); c->offsets.release(); c->cursor.release();
     c->large_ids.release(); c->entries.release(); c->dstats.release();
     c->item_counts.release(); c->item_offsets.release(); c->items.release();
@@ -433,6 +444,13 @@ static FrameConst make_frame(const spl_ctx *c, const spl_camera &cam) {
     fc.r_sml2 = (float)(q.r_sml * q.r_sml);
     fc.r_small2 = (float)(q.r_small * q.r_small);
     fc.r_large2 = (float)(q.r_large * q.r_large);
+    fc.absorb = q.mode == SPL_MODE_ABSORB ? 1 : 0;
+    fc.absorption = (float)q.absorption;
+    if (fc.absorb) {
+        // one list per tile: no small class, no separate large pass
+        fc.r_small2 = fc.r_sml2;
+        fc.r_large2 = 3.0e38f;
+    }
     fc.s_min = c->s_min;
     fc.s_inv = c->s_max != c->s_min ? (float)(1.0 / ((double)c->s_max - (double)c->s_min)) : 0.f;
     fc.brightness = (float)q.brightness;
@@ -488,6 +506,12 @@ static int prepare_views(spl_ctx *c, const spl_camera *cams, int V, float *const
     const size_t recs = (size_t)V * (size_t)src_n(c);
     SPL_TRY(grow(c, c->rec0, recs ? recs : 1));
     SPL_TRY(grow(c, c->rec1, recs ? recs : 1));
+    if (c->par.mode == SPL_MODE_ABSORB) {
+        SPL_TRY(grow(c, c->rec2, recs ? recs : 1));
+        SPL_TRY(grow(c, c->pkeys, recs ? recs : 1));
+        SPL_TRY(grow(c, c->ptmp, recs ? recs : 1));
+        SPL_TRY(grow(c, c->rank, recs ? recs : 1));
+    }
     SPL_TRY(grow(c, c->large_ids, recs ? recs : 1));
     SPL_TRY(grow(c, c->counts, (size_t)NLIST * tiles));
     SPL_TRY(grow(c, c->offsets, (size_t)NLIST * tiles + 1));
@@ -536,6 +560,7 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
     }
     ra.pal = c->pal.p;
     ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
+    ra.rec2 = c->par.mode == SPL_MODE_ABSORB ? c->rec2.p : nullptr;
     ra.counts = c->counts.p;
     ra.large_ids = c->large_ids.p;
     ra.st = c->dstats.p;
@@ -592,6 +617,21 @@ static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
         ta.order = c->order.p;
     }
     if (c->recording) ta.item_cycles = c->item_cycles.p;
+    if (c->par.mode == SPL_MODE_ABSORB) {
+        // one view: every entry sits in the medium slots [L_MEDIUM * nt, (L_MEDIUM + 1) * nt]
+        const int nt = c->h_fcs[0].ntiles;
+        launch_depth_order(c->rec1.p, c->rec2.p, vs.n, c->entries.p, c->offsets.p + L_MEDIUM * nt,
+                           nt, (long long)c->hstats->slot_total, c->pkeys.p, c->ptmp.p,
+                           c->ekeys.p, c->etmp.p, c->rank.p, c->sort_hist.p, c->sms, s);
+        ta.rec2 = c->rec2.p;
+        ta.partial = c->partial.p;
+        record_event(c, 2, s);
+        launch_absorb_pass(vs, ta, c->item_offsets.p, c->sms, s);
+        record_event(c, 3, s);
+        record_event(c, 4, s);
+        record_event(c, 5, s);
+        return;
+    }
     record_event(c, 2, s);
     launch_tile_pass(vs, ta, c->sms, s);
     record_event(c, 3, s);
@@ -641,6 +681,13 @@ static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const 
     SPL_TRY(grow(c, c->entries, (size_t)(total ? total : 1)));
     SPL_TRY(grow(c, c->items, (size_t)(n_tile_items + n_large_items + 1)));
     SPL_TRY(size_item_buffers(c));
+    if (c->par.mode == SPL_MODE_ABSORB) {
+        const int64_t m = total > vs.n ? total : vs.n;
+        SPL_TRY(grow(c, c->ekeys, (size_t)(total ? total : 1)));
+        SPL_TRY(grow(c, c->etmp, (size_t)(total ? total : 1)));
+        SPL_TRY(grow(c, c->sort_hist, (size_t)512 * (size_t)radix_blocks(m > 0 ? m : 1) + 2));
+        SPL_TRY(grow(c, c->partial, c->items.cap * (size_t)vs.tile * (size_t)vs.tile));
+    }
     c->last_items = n_tile_items + n_large_items;
     enqueue_render(c, vs, n_large_items > 0, s);
     SPL_CUDA(cudaGetLastError());
@@ -715,6 +762,7 @@ extern "C" int spl_render_stream(spl_ctx *c, const spl_particles *p, int64_t chu
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
     if (!c->have_cam) return SPL_ESTATE;
     if (c->npal < 1) return SPL_ESTATE;
+    if (c->par.mode == SPL_MODE_ABSORB) return SPL_EINVAL;   // not additive over chunks
     DeviceGuard g(c->device);
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     if (!c->copy_stream) {
@@ -839,6 +887,7 @@ extern "C" int spl_render_batch(spl_ctx *c, const spl_camera *cams, int32_t n_vi
         if (!camera_ok(&cams[v]) || !d_images[v]) return SPL_EINVAL;
     if (n_views == 0) return SPL_OK;
     if (!c->have_particles || c->npal < 1) return SPL_ESTATE;
+    if (c->par.mode == SPL_MODE_ABSORB) return SPL_EINVAL;   // single views only
     DeviceGuard g(c->device);
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     const unsigned long long key = batch_key(c, cams, n_views);
@@ -897,6 +946,7 @@ extern "C" int spl_autotune(spl_ctx *c, const spl_camera *cams, int32_t n_views,
     for (int v = 0; v < n_views; ++v)
         if (!camera_ok(&cams[v]) || !d_images[v]) return SPL_EINVAL;
     if (!c->have_particles || c->npal < 1) return SPL_ESTATE;
+    if (c->par.mode == SPL_MODE_ABSORB) return SPL_EINVAL;   // single views only
     DeviceGuard g(c->device);
     static const int tiles[] = {16, 32, 64};
     static const double radii[][2] = {{0.0, 32.0}, {0.0, 64.0}, {0.0, 128.0}, {0.0, 1e9}, {2.0, 64.0}};
@@ -1191,7 +1241,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
         if (!std::isfinite(rgb[k])) return SPL_EINVAL;
     spl_ctx tmp;   // parameters only; none of its buffers is allocated
     if (q) {
-        if (!params_ok(q)) return SPL_EINVAL;
+        if (!params_ok(q) || q->mode == SPL_MODE_ABSORB) return SPL_EINVAL;
         tmp.par = *q;
     } else {
         spl_default_params(&tmp.par);

@@ -50,6 +50,8 @@ struct FrameConst {
     int view;                  // index in the batch
     int tile_base;             // first global tile: global tile = tile_base + local tile
     int slot_base;             // first list slot: slot = slot_base + list * ntiles + tile
+    int absorb;                // general absorption (Eq. 1, E != A): one depth-sorted list per tile
+    float absorption;          // A = absorption * brightness * I
     int pad_;
     long long rec_base;        // first record: record = rec_base + particle id
 };
@@ -103,6 +105,7 @@ struct RasterArgs {
     const void *h, *I, *s;
     const float *pal;          // npal * 3
     float4 *rec0, *rec1;       // nviews * n records
+    float2 *rec2;              // absorption mode: (A, depth key) per record, else null
     int *counts;               // list slots of all views
     unsigned *large_ids;       // record indices, capacity nviews * n
     DevStats *st;
@@ -129,6 +132,8 @@ struct TileArgs {
     const int *order;          // optional: processing order of each pass's items
     long long *item_cycles;    // optional: SM clock cycles spent on each item
     int accumulate;            // add into the images instead of storing (streamed chunks)
+    const float2 *rec2;        // absorption mode: per record (A, depth key)
+    float4 *partial;           // absorption mode: (C, T) per pixel of every split item
 };
 
 // Tile-cost network 32 -> 64 (ReLU) -> 1; parameter vector layout
@@ -155,6 +160,15 @@ void launch_fill_items(const Views &v, const long long *offsets, const int *item
 void launch_scatter(const Views &v, const BinArgs &a, int sms, cudaStream_t s);
 void launch_tile_pass(const Views &v, const TileArgs &a, int sms, cudaStream_t s);
 void launch_large_pass(const Views &v, const TileArgs &a, int sms, cudaStream_t s);
+// Absorption mode: the depth-ordered pass and the composition of split tiles.
+void launch_absorb_pass(const Views &v, const TileArgs &a, const int *item_offsets, int sms,
+                        cudaStream_t s);
+int radix_blocks(int64_t n);
+void launch_depth_order(const float4 *rec1, const float2 *rec2, int64_t n, unsigned *entries,
+                        const long long *off, int ntiles, long long total, unsigned long long *pkeys,
+                        unsigned long long *ptmp, unsigned long long *ekeys,
+                        unsigned long long *etmp, unsigned *rank, int *hist, int sms,
+                        cudaStream_t s);
 void launch_epilogue_ea(float *image, int64_t nvals, int sms, cudaStream_t s);
 // Zero every view's image / apply the E=A map to every view's image (the
 // image pointers are read from device memory, so a graph can replay them).

@@ -73,10 +73,13 @@ __device__ __forceinline__ float load_attr(const void *p, int64_t i) {
     return static_cast<const float *>(p)[i];
 }
 
-// Rasterise one particle into its record; returns its class.
+// Rasterise one particle into its record; returns its class.  q2 receives
+// (absorption coefficient A, depth key) for the absorption mode: A =
+// absorption * brightness * I, the key z_c rounded to float (the double-float
+// value's leading part).
 __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spal, float x, float y,
                                           float z, float h, float inten, float s, float4 &r0,
-                                          float4 &r1) {
+                                          float4 &r1, float2 &q2) {
     // roto-translation x_c = R x - R eye, in df
     df c[3];
 #pragma unroll
@@ -88,6 +91,7 @@ __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spa
     }
     r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
+    q2 = make_float2(0.f, 0.f);
     // non-finite inputs or a negative smoothing length: inactive
     if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(h) || !isfinite(inten) ||
         !isfinite(s) || h < 0.f)
@@ -127,20 +131,25 @@ __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spa
         return CLS_INACTIVE;
     r0 = make_float4(pack_xy(xi, yi), xf, yf, 1.4426950408889634f / (sig * sig));
     r1 = make_float4(r * r, amp * col[0], amp * col[1], amp * col[2]);
+    q2 = make_float2(fc.absorption * amp, zc);
     return record_class(fc, r1.x);
 }
 
 // Tile footprint of one rasterised particle for the point / small / medium
 // lists: a box of tiles [tx0, tx0 + bw) x [ty0, ty0 + nbox / bw) (nbox = 0:
-// no entry).  Large particles are handled by large_tiles_kernel.
-struct TileFoot { int list, tx0, ty0, bw, nbox; };
+// no entry); disc = 1 when a tile of the box must also be reached by the disc.
+// Large particles are handled by large_tiles_kernel.  In the absorption mode
+// points join the medium list, so that a tile's particles form one list that
+// can be ordered by depth.
+struct TileFoot { int list, tx0, ty0, bw, nbox, disc; };
 
 __device__ __forceinline__ TileFoot tile_footprint(const FrameConst &fc, int cls, float4 r0, float4 r1) {
-    TileFoot f{-1, 0, 0, 1, 0};
+    TileFoot f{-1, 0, 0, 1, 0, 0};
     if (cls == CLS_POINT) {
         const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
         if (xi >= 0 && yi >= 0 && xi < fc.width && yi < fc.height) {
-            f.list = L_POINT; f.tx0 = xi / fc.tile; f.ty0 = yi / fc.tile; f.nbox = 1;
+            f.list = fc.absorb ? L_MEDIUM : L_POINT;
+            f.tx0 = xi / fc.tile; f.ty0 = yi / fc.tile; f.nbox = 1;
         }
         return f;
     }
@@ -148,6 +157,7 @@ __device__ __forceinline__ TileFoot tile_footprint(const FrameConst &fc, int cls
     PixBox b;
     if (!splat_box(fc, r0, r1.x, b)) return f;
     f.list = cls == CLS_SMALL ? L_SMALL : L_MEDIUM;
+    f.disc = 1;
     f.tx0 = b.i0 / fc.tile;
     f.ty0 = b.j0 / fc.tile;
     f.bw = b.i1 / fc.tile - f.tx0 + 1;
@@ -161,7 +171,7 @@ __device__ __forceinline__ int foot_slot(const FrameConst &fc, const TileFoot &f
                                          float4 r1) {
     if (k >= f.nbox) return -1;
     const int tx = f.tx0 + k % f.bw, ty = f.ty0 + k / f.bw;
-    if (f.list != L_POINT && !disc_meets_tile(fc, r0, r1.x, tx, ty)) return -1;
+    if (f.disc && !disc_meets_tile(fc, r0, r1.x, tx, ty)) return -1;
     return f.list * fc.ntiles + ty * fc.ntx + tx;
 }
 
@@ -264,12 +274,15 @@ __global__ void __launch_bounds__(256) raster_kernel(Views vs, RasterArgs a) {
             float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
             const int64_t rec = fc.rec_base + i;
             if (valid) {
+                float2 q2;
                 cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_attr<ATTR == 1>(a.h, i),
-                                 load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i), r0, r1);
+                                 load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i), r0, r1,
+                                 q2);
                 a.rec0[rec] = r0;
                 a.rec1[rec] = r1;
+                if (a.rec2) a.rec2[rec] = q2;
             }
-            const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0};
+            const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0, 0};
             const int maxk = __reduce_max_sync(0xffffffffu, foot.nbox);
             for (int k = 0; k < maxk; ++k) {
                 const int ls = foot_slot(fc, foot, k, r0, r1);
@@ -517,10 +530,10 @@ __device__ __forceinline__ TileFoot load_foot(const FrameConst &fc, const BinArg
                                               bool valid, float4 &r0, float4 &r1) {
     r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
-    if (!valid) return TileFoot{-1, 0, 0, 1, 0};
+    if (!valid) return TileFoot{-1, 0, 0, 1, 0, 0};
     r1 = a.rec1[rec];
     const int cls = record_class(fc, r1.x);
-    if (cls == CLS_INACTIVE || cls == CLS_LARGE) return TileFoot{-1, 0, 0, 1, 0};
+    if (cls == CLS_INACTIVE || cls == CLS_LARGE) return TileFoot{-1, 0, 0, 1, 0, 0};
     r0 = a.rec0[rec];
     return tile_footprint(fc, cls, r0, r1);
 }

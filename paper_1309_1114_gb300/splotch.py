@@ -40,7 +40,7 @@ class spl_params(C.Structure):
     _fields_ = [("chi", C.c_double), ("sigma_per_h", C.c_double), ("s_box", C.c_double),
                 ("r_sml", C.c_double), ("brightness", C.c_double), ("tile_px", C.c_int32),
                 ("r_small", C.c_double), ("r_large", C.c_double), ("mode", C.c_int32),
-                ("sched", C.c_int32)]
+                ("sched", C.c_int32), ("absorption", C.c_double)]
 
 
 class spl_stats(C.Structure):
