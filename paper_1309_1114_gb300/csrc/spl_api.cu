@@ -685,7 +685,7 @@ static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const 
         const int64_t m = total > vs.n ? total : vs.n;
         SPL_TRY(grow(c, c->ekeys, (size_t)(total ? total : 1)));
         SPL_TRY(grow(c, c->etmp, (size_t)(total ? total : 1)));
-        SPL_TRY(grow(c, c->sort_hist, (size_t)512 * (size_t)radix_blocks(m > 0 ? m : 1) + 2));
+        SPL_TRY(grow(c, c->sort_hist, (size_t)radix_scratch_ints(m)));
         SPL_TRY(grow(c, c->partial, c->items.cap * (size_t)vs.tile * (size_t)vs.tile));
     }
     c->last_items = n_tile_items + n_large_items;

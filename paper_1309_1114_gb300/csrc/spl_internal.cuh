@@ -164,6 +164,7 @@ void launch_large_pass(const Views &v, const TileArgs &a, int sms, cudaStream_t 
 void launch_absorb_pass(const Views &v, const TileArgs &a, const int *item_offsets, int sms,
                         cudaStream_t s);
 int radix_blocks(int64_t n);
+int64_t radix_scratch_ints(int64_t n);
 void launch_depth_order(const float4 *rec1, const float2 *rec2, int64_t n, unsigned *entries,
                         const long long *off, int ntiles, long long total, unsigned long long *pkeys,
                         unsigned long long *ptmp, unsigned long long *ekeys,

@@ -96,19 +96,101 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const unsig
 
 int radix_blocks(int64_t n) { return (int)((n + kSortTile - 1) / kSortTile); }
 
+// Exclusive scan of m ints for the digit table: blocks of kScanChunk values
+// are reduced, the block sums scanned by one CTA (scan_kernel), and every
+// block then scans its values from its base.  out[m] = total.
+constexpr int kScanThreads = 1024, kScanPer = 8, kScanChunk = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int block_exclusive(int v, int *wsum, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = wsum[lane];
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        wsum[lane] = wi - w;
+        if (lane == 31) wsum[32] = wi;
+    }
+    __syncthreads();
+    total = wsum[32];
+    const int r = wsum[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int *in, int m, int *part) {
+    __shared__ int wsum[33];
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < m) v += in[base + k];
+    int total;
+    block_exclusive(v, wsum, total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int *in, int m,
+                                                                  const int *pbase, int nparts,
+                                                                  int *out) {
+    __shared__ int wsum[33];
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    int v[kScanPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = base + k < m ? in[base + k] : 0;
+        sum += v[k];
+    }
+    int total;
+    int run = pbase[blockIdx.x] + block_exclusive(sum, wsum, total);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < m) out[base + k] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = pbase[nparts];
+}
+
+static int scan_parts(int m) { return (m + kScanChunk - 1) / kScanChunk; }
+
+// Ints of radix scratch for n keys: digit counts, scanned bases, block sums.
+int64_t radix_scratch_ints(int64_t n) {
+    const int64_t nb = radix_blocks(n > 0 ? n : 1);
+    const int64_t parts = scan_parts((int)(256 * nb));
+    return 512 * nb + 2 + 2 * (parts + 1);
+}
+
+static void scan_digits(int m, const int *in, int *out, int *part, int *pbase, cudaStream_t s) {
+    const int np = scan_parts(m);
+    scan_reduce_kernel<<<np, kScanThreads, 0, s>>>(in, m, part);
+    launch_scan(np, part, pbase, nullptr, 0, nullptr, s);
+    scan_apply_kernel<<<np, kScanThreads, 0, s>>>(in, m, pbase, np, out);
+}
+
 // Sorts keys[0, n) by the 8-bit digits at the given shifts (least
-// significant first); tmp holds n keys; hist holds 256 * radix_blocks(n) + 1
-// ints (twice: counts and scanned bases).  Returns the array holding the
-// result (keys or tmp).
+// significant first); tmp holds n keys; hist holds radix_scratch_ints(n)
+// ints.  Returns the array holding the result (keys or tmp).
 unsigned long long *launch_radix_sort(unsigned long long *keys, unsigned long long *tmp, int64_t n,
                                       const int *shifts, int npasses, int *hist, cudaStream_t s) {
     if (n <= 0) return keys;
     const int nb = radix_blocks(n);
-    int *cnt = hist, *bases = hist + 256 * nb + 1;
+    const int m = 256 * nb, np = scan_parts(m);
+    int *cnt = hist, *bases = hist + m + 1, *part = bases + m + 1, *pbase = part + np + 1;
     unsigned long long *a = keys, *b = tmp;
     for (int p = 0; p < npasses; ++p) {
         radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(a, n, shifts[p], cnt, nb);
-        launch_scan(256 * nb, cnt, bases, nullptr, 0, nullptr, s);
+        scan_digits(m, cnt, bases, part, pbase, s);
         radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(a, b, n, shifts[p], bases, nb);
         unsigned long long *t = a;
         a = b;
@@ -181,7 +263,7 @@ static int bits_for(unsigned long long v) {
 // slots off[0 .. ntiles] (device offsets into entries; the host passes their
 // total, off[ntiles] - off[0], known after the binning synchronisation).
 // pkeys/ptmp: n particle keys each; ekeys/etmp: total entry keys each;
-// rank: n; hist: 512 * radix_blocks(max(n, total)) + 1 ints.
+// rank: n; hist: radix_scratch_ints(max(n, total)) ints.
 void launch_depth_order(const float4 *rec1, const float2 *rec2, int64_t n, unsigned *entries,
                         const long long *off, int ntiles, long long total, unsigned long long *pkeys,
                         unsigned long long *ptmp, unsigned long long *ekeys,
