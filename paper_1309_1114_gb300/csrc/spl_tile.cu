@@ -296,14 +296,20 @@ __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp
     }
 }
 
-// Dynamic shared memory of one CTA (bytes), in this order: srow, st0, st1,
-// swx, sacc.
+// Dynamic shared memory of one CTA (bytes): the batch tables srow and swx,
+// then the staged records st0, st1.  The shared tile sacc of the point and
+// small passes (3 T^2 floats) reuses the table space: those passes run after
+// the medium list, when the tables are no longer read.
 template <int T>
-constexpr size_t smem_bytes() {
+__host__ __device__ constexpr size_t table_bytes() {
     using S = Shape<T>;
-    return sizeof(float4) * (S::P * T + 2 * kTileThreads) + sizeof(float2) * S::P * T +
-           sizeof(float) * 3 * T * T;
+    return (sizeof(float4) + sizeof(float2)) * S::P * T;
 }
+static_assert(table_bytes<16>() >= sizeof(float) * 3 * 16 * 16, "shared tile fits the tables");
+static_assert(table_bytes<32>() >= sizeof(float) * 3 * 32 * 32, "shared tile fits the tables");
+static_assert(table_bytes<64>() >= sizeof(float) * 3 * 64 * 64, "shared tile fits the tables");
+template <int T>
+__host__ __device__ constexpr size_t smem_bytes() { return table_bytes<T>() + sizeof(float4) * 2 * kTileThreads; }
 
 template <int T>
 constexpr int min_ctas() { return T >= 64 ? 2 : (T == 32 ? 5 : 4); }
@@ -317,10 +323,10 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
     constexpr int NW = kTileThreads / 32;
     extern __shared__ float4 smem_raw[];
     float4 (*srow)[T] = reinterpret_cast<float4 (*)[T]>(smem_raw);
-    float4 *st0 = smem_raw + S::P * T;
+    float2 (*swx)[T] = reinterpret_cast<float2 (*)[T]>(smem_raw + S::P * T);
+    float (*sacc)[T][T] = reinterpret_cast<float (*)[T][T]>(smem_raw);   // after the tables
+    float4 *st0 = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + table_bytes<T>());
     float4 *st1 = st0 + kTileThreads;
-    float2 (*swx)[T] = reinterpret_cast<float2 (*)[T]>(st1 + kTileThreads);
-    float (*sacc)[T][T] = reinterpret_cast<float (*)[T][T]>(&swx[S::P][0]);
     __shared__ unsigned band_mask[NW];
     __shared__ int s_item;
     __shared__ FrameConst sfc;
@@ -331,7 +337,6 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
     for (;;) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(counter, 1);
-        for (int k = tid; k < 3 * T * T; k += kTileThreads) (&sacc[0][0][0])[k] = 0.f;
         __syncthreads();
         const int it = s_item;
         if (it >= n_items) break;
@@ -366,32 +371,6 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
         Acc<T> acc;
         acc.zero();
 
-        // points (Sec. 4.1): batches of 256 staged records, warp-aggregated
-#pragma unroll 1
-        for (long long base = lb0; base < le0; base += kTileThreads) {
-            const int cnt = (int)(le0 - base < kTileThreads ? le0 - base : kTileThreads);
-            if (tid < cnt) {
-                const unsigned id = a.entries[base + tid];
-                st0[tid] = a.rec0[id];
-                st1[tid] = a.rec1[id];
-            }
-            __syncthreads();
-            warp_points<T>(a, st0 + warp * 32, st1 + warp * 32, cnt - warp * 32, x0, y0, sacc, lane);
-            __syncthreads();
-        }
-        // small particles: one warp each over the pixel box
-#pragma unroll 1
-        for (long long base = lb1; base < le1; base += kTileThreads) {
-            const int cnt = (int)(le1 - base < kTileThreads ? le1 - base : kTileThreads);
-            if (tid < cnt) {
-                const unsigned id = a.entries[base + tid];
-                st0[tid] = a.rec0[id];
-                st1[tid] = a.rec1[id];
-            }
-            __syncthreads();
-            for (int k = warp; k < cnt; k += NW) warp_small<T>(fc, st0[k], st1[k], x0, y0, sacc, lane);
-            __syncthreads();
-        }
         // medium (or large) particles: tabulate a batch, then every row band
         // adds it; the next batch's records are fetched into registers while
         // the current one is processed
@@ -427,6 +406,40 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
             __syncthreads();
         }
 
+        // points and small particles go through the shared tile, which reuses
+        // the table space (the tables are dead once every warp is past here)
+        const bool shared_tile = le0 > lb0 || le1 > lb1;
+        if (shared_tile) {
+            __syncthreads();
+            for (int k = tid; k < 3 * T * T; k += kTileThreads) (&sacc[0][0][0])[k] = 0.f;
+            __syncthreads();
+        }
+        // points (Sec. 4.1): batches of 256 staged records, warp-aggregated
+#pragma unroll 1
+        for (long long base = lb0; base < le0; base += kTileThreads) {
+            const int cnt = (int)(le0 - base < kTileThreads ? le0 - base : kTileThreads);
+            if (tid < cnt) {
+                const unsigned id = a.entries[base + tid];
+                st0[tid] = a.rec0[id];
+                st1[tid] = a.rec1[id];
+            }
+            __syncthreads();
+            warp_points<T>(a, st0 + warp * 32, st1 + warp * 32, cnt - warp * 32, x0, y0, sacc, lane);
+            __syncthreads();
+        }
+        // small particles: one warp each over the pixel box
+#pragma unroll 1
+        for (long long base = lb1; base < le1; base += kTileThreads) {
+            const int cnt = (int)(le1 - base < kTileThreads ? le1 - base : kTileThreads);
+            if (tid < cnt) {
+                const unsigned id = a.entries[base + tid];
+                st0[tid] = a.rec0[id];
+                st1[tid] = a.rec1[id];
+            }
+            __syncthreads();
+            for (int k = warp; k < cnt; k += NW) warp_small<T>(fc, st0[k], st1[k], x0, y0, sacc, lane);
+            __syncthreads();
+        }
         // write: shared part + registers, stored (only item of its tile; added
         // to the previous chunks' sum when accumulating) or added atomically
         const bool store = !LARGE && list < 0;
@@ -441,7 +454,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
                 float *dst = image + 3 * ((int64_t)(y0 + row) * fc.width + x0 + cx);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float v = sacc[c][row][cx] + acc.get(q, k, c);
+                    const float v = (shared_tile ? sacc[c][row][cx] : 0.f) + acc.get(q, k, c);
                     if (store)
                         dst[c] = a.accumulate ? dst[c] + v : v;
                     else if (v != 0.f)
