@@ -186,12 +186,13 @@ __device__ __forceinline__ int foot_slot(const FrameConst &fc, const TileFoot &f
 // never emptied while a CTA runs, so that choice is the same for every
 // occurrence of the key within the CTA.
 // ---------------------------------------------------------------------------
-constexpr int kHash = 4096;          // slots (power of two)
+constexpr int kHashBits = 11;
+constexpr int kHash = 1 << kHashBits; // slots
 constexpr int kProbe = 32;
-constexpr int kChunk = 4096;         // particles per CTA in the binning kernels
+constexpr int kChunk = 2048;         // particles per CTA in the binning kernels
 
 __device__ __forceinline__ int hash_slot(const int *keys, int key, bool insert) {
-    unsigned h = ((unsigned)key * 2654435761u) >> 20;
+    unsigned h = ((unsigned)key * 2654435761u) >> (32 - kHashBits);
     for (int probe = 0; probe < kProbe; ++probe) {
         const int slot = (int)((h + (unsigned)probe) & (kHash - 1));
         const int k = *(volatile const int *)&keys[slot];
@@ -250,7 +251,7 @@ __device__ __forceinline__ void load_view(const FrameConst *fcs, int v, FrameCon
 // ATTR: 0 = h, I, s in FP32; 1 = all three in binary16; 2 = h in FP32, I and s
 // in binary16.
 template <int ATTR>
-__global__ void __launch_bounds__(256) raster_kernel(Views vs, RasterArgs a) {
+__global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) {
     __shared__ float spal[3 * kMaxPalette];
     __shared__ int keys[kHash], vals[kHash];
     __shared__ unsigned long long bstat[5];
