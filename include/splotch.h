@@ -292,7 +292,7 @@ int spl_get_records(spl_ctx *ctx, int64_t n, double *xs, double *ys, float *r,
  * memory budget the caller owns, or in a host application that passes only
  * its own buffers).  It needs no context.  It runs the kernels of
  * spl_render, with every scratch buffer carved from one file-scope
- * __device__ array of about 15 MiB that each GPU loading the library holds
+ * __device__ array of about 16 MiB that each GPU loading the library holds
  * until the process exits.  The paper has no counterpart: it is a property
  * of this library, not of the method.
  *   p       particles in DEVICE memory (mem_space must be SPL_MEM_DEVICE),

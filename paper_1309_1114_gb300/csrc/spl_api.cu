@@ -90,7 +90,8 @@ struct spl_ctx {
     DevBuf<unsigned> rank;
     DevBuf<int> sort_hist;
     DevBuf<float4> partial;
-    DevBuf<int> counts;
+    DevBuf<int> counts, ovf;
+    DevBuf<int2> ctab;
     DevBuf<long long> offsets, cursor;
     DevBuf<unsigned> large_ids, entries;
     DevBuf<int> item_counts, item_offsets;
@@ -262,6 +263,7 @@ extern "C" int spl_destroy(spl_ctx *c) {
     c->rec2.release(); c->pkeys.release(); c->ptmp.release(); c->ekeys.release();
     c->etmp.release(); c->rank.release(); c->sort_hist.release(); c->partial.release();
     c->counts.release(); c->offsets.release(); c->cursor.release();
+    c->ovf.release(); c->ctab.release();
     c->large_ids.release(); c->entries.release(); c->dstats.release();
     c->item_counts.release(); c->item_offsets.release(); c->items.release();
     c->host_img_scratch.release();
@@ -514,6 +516,8 @@ static int prepare_views(spl_ctx *c, const spl_camera *cams, int V, float *const
     }
     SPL_TRY(grow(c, c->large_ids, recs ? recs : 1));
     SPL_TRY(grow(c, c->counts, (size_t)NLIST * tiles));
+    SPL_TRY(grow(c, c->ovf, (size_t)NLIST * tiles));
+    SPL_TRY(grow(c, c->ctab, (size_t)ctab_entries(src_n(c), V)));
     SPL_TRY(grow(c, c->offsets, (size_t)NLIST * tiles + 1));
     SPL_TRY(grow(c, c->cursor, (size_t)NLIST * tiles));
     SPL_TRY(grow(c, c->item_counts, (size_t)2 * tiles));
@@ -547,6 +551,7 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
     cudaMemcpyAsync(c->d_fcs.p, c->h_fcs, sizeof(FrameConst) * vs.nviews, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(c->d_images.p, c->h_images, sizeof(float *) * vs.nviews, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(c->counts.p, 0, sizeof(int) * NLIST * vs.total_tiles, s);
+    cudaMemsetAsync(c->ovf.p, 0, sizeof(int) * NLIST * vs.total_tiles, s);
     cudaMemsetAsync(c->dstats.p, 0, offsetof(DevStats, err), s);
     RasterArgs ra{};
     ra.n = src_n(c);
@@ -562,6 +567,8 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
     ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
     ra.rec2 = c->par.mode == SPL_MODE_ABSORB ? c->rec2.p : nullptr;
     ra.counts = c->counts.p;
+    ra.ovf = c->ovf.p;
+    ra.ctab = c->ctab.p;
     ra.large_ids = c->large_ids.p;
     ra.st = c->dstats.p;
     launch_raster(vs, ra, c->streaming ? c->chunk_attr : c->attr_type, s);
@@ -570,11 +577,12 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
     ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
     ba.large_ids = c->large_ids.p;
     ba.counts = c->counts.p;
+    ba.ovf = c->ovf.p;
     ba.cursor = c->cursor.p;
     ba.st = c->dstats.p;
     launch_count_large(vs, ba, c->sms, s);
-    launch_scan(NLIST * vs.total_tiles, c->counts.p, c->offsets.p, c->cursor.p, 1,
-                &c->dstats.p->slot_total, s);
+    launch_slot_offsets(NLIST * vs.total_tiles, c->counts.p, c->ovf.p, c->offsets.p, c->cursor.p,
+                        &c->dstats.p->slot_total, s);
     launch_item_counts(vs, c->offsets.p, c->item_counts.p, c->dstats.p, s);
     launch_scan(2 * vs.total_tiles, c->item_counts.p, c->item_offsets.p, nullptr, 2,
                 c->dstats.p->item_totals, s);
@@ -587,6 +595,9 @@ static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
     ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
     ba.large_ids = c->large_ids.p;
     ba.counts = c->counts.p;
+    ba.ovf = c->ovf.p;
+    ba.offsets = c->offsets.p;
+    ba.ctab = c->ctab.p;
     ba.cursor = c->cursor.p;
     ba.entries = c->entries.p;
     ba.entries_cap = (int64_t)c->entries.cap;
@@ -1194,7 +1205,9 @@ constexpr size_t kNaOffsets = kNaCounts + na_round(sizeof(int) * NLIST * kNaMaxT
 constexpr size_t kNaCursor = kNaOffsets + na_round(sizeof(long long) * (NLIST * kNaMaxTiles + 1));
 constexpr size_t kNaItemCounts = kNaCursor + na_round(sizeof(long long) * NLIST * kNaMaxTiles);
 constexpr size_t kNaItemOffsets = kNaItemCounts + na_round(sizeof(int) * 2 * kNaMaxTiles);
-constexpr size_t kNaEntries = kNaItemOffsets + na_round(sizeof(int) * (2 * kNaMaxTiles + 1));
+constexpr size_t kNaOvf = kNaItemOffsets + na_round(sizeof(int) * (2 * kNaMaxTiles + 1));
+constexpr size_t kNaCtab = kNaOvf + na_round(sizeof(int) * NLIST * kNaMaxTiles);
+constexpr size_t kNaEntries = kNaCtab + na_round(sizeof(int2) * ctab_entries(kNaMaxParticles, 1));
 constexpr size_t kNaItems = kNaEntries + na_round(sizeof(unsigned) * kNaMaxEntries);
 constexpr size_t kNaView = kNaItems + na_round(sizeof(WorkItem) * kNaMaxItems);
 constexpr size_t kNaImage = kNaView + na_round(sizeof(FrameConst));
@@ -1270,6 +1283,8 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     long long *cursor = reinterpret_cast<long long *>(base + kNaCursor);
     int *item_counts = reinterpret_cast<int *>(base + kNaItemCounts);
     int *item_offsets = reinterpret_cast<int *>(base + kNaItemOffsets);
+    int *ovf = reinterpret_cast<int *>(base + kNaOvf);
+    int2 *ctab = reinterpret_cast<int2 *>(base + kNaCtab);
     unsigned *entries = reinterpret_cast<unsigned *>(base + kNaEntries);
     WorkItem *items = reinterpret_cast<WorkItem *>(base + kNaItems);
     FrameConst *d_fc = reinterpret_cast<FrameConst *>(base + kNaView);
@@ -1295,6 +1310,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     SPL_CUDA(cudaMemcpyAsync(d_img, &d_image, sizeof(float *), cudaMemcpyHostToDevice, s));
     SPL_CUDA(cudaMemsetAsync(dst, 0, sizeof(DevStats), s));
     SPL_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * NLIST * fc.ntiles, s));
+    SPL_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int) * NLIST * fc.ntiles, s));
     RasterArgs ra{};
     ra.n = p->n;
     ra.x = p->x; ra.y = p->y; ra.z = p->z;
@@ -1302,6 +1318,8 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     ra.pal = pal;
     ra.rec0 = rec0; ra.rec1 = rec1;
     ra.counts = counts;
+    ra.ovf = ovf;
+    ra.ctab = ctab;
     ra.large_ids = large_ids;
     ra.st = dst;
     launch_raster(vs, ra, p->attr_type, s);
@@ -1309,10 +1327,13 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     ba.rec0 = rec0; ba.rec1 = rec1;
     ba.large_ids = large_ids;
     ba.counts = counts;
+    ba.ovf = ovf;
+    ba.offsets = offsets;
+    ba.ctab = ctab;
     ba.cursor = cursor;
     ba.st = dst;
     launch_count_large(vs, ba, sms, s);
-    launch_scan(NLIST * fc.ntiles, counts, offsets, cursor, 1, &dst->slot_total, s);
+    launch_slot_offsets(NLIST * fc.ntiles, counts, ovf, offsets, cursor, &dst->slot_total, s);
     launch_item_counts(vs, offsets, item_counts, dst, s);
     launch_scan(2 * fc.ntiles, item_counts, item_offsets, nullptr, 2, dst->item_totals, s);
     SPL_CUDA(cudaGetLastError());

@@ -99,6 +99,17 @@ __host__ __device__ inline int item_list(const WorkItem &w) {
 // tile (a halo core holding 1e5-1e6 particles) is spread over many CTAs.
 constexpr int kSegPoint = 8192, kSegSmall = 2048, kSegMedium = 1024, kSegLarge = 512;
 
+// Binning CTAs: each takes kChunk consecutive particles and aggregates their
+// list slots in a shared-memory hash table of kHash slots, which the scatter
+// reuses (one table per CTA and view).
+constexpr int kHashBits = 11;
+constexpr int kHash = 1 << kHashBits;
+constexpr int kChunk = 2048;
+__host__ __device__ constexpr int64_t ctab_entries(int64_t n, int nviews) {
+    return ((n + kChunk - 1) / kChunk > 0 ? (n + kChunk - 1) / kChunk : 1) *
+           (nviews > 0 ? nviews : 1) * kHash;
+}
+
 struct RasterArgs {
     int64_t n;
     const float *x, *y, *z;
@@ -106,16 +117,26 @@ struct RasterArgs {
     const float *pal;          // npal * 3
     float4 *rec0, *rec1;       // nviews * n records
     float2 *rec2;              // absorption mode: (A, depth key) per record, else null
-    int *counts;               // list slots of all views
+    int *counts;               // list slots of all views: entries counted through the CTA tables
+    int *ovf;                  // list slots: entries placed through the cursors (see BinArgs)
+    int2 *ctab;                // per (CTA, view): the CTA hash table, (slot, offset in the slot)
     unsigned *large_ids;       // record indices, capacity nviews * n
     DevStats *st;
 };
 
+// A list slot's range [offsets[k], offsets[k+1]) holds first the entries
+// whose place the rasteriser's CTA tables fixed (counts[k] of them: CTA b's
+// share starts at offsets[k] + its table's offset), then the entries placed
+// one warp group at a time through cursor[k] = offsets[k] + counts[k]: those
+// of keys that found no room in a CTA table, and the large list (ovf[k]).
 struct BinArgs {
     const float4 *rec0, *rec1;
     const unsigned *large_ids;
-    long long *cursor;         // list slots, starts as the offsets
+    long long *cursor;         // list slots, starts at offsets + counts
     int *counts;
+    int *ovf;
+    const long long *offsets;
+    const int2 *ctab;
     unsigned *entries;         // record indices
     int64_t entries_cap;
     DevStats *st;
@@ -146,6 +167,10 @@ constexpr int kNParam = kHid * kFeat + 2 * kHid + 1;
 // the whole sequence can be captured in a CUDA graph.
 void launch_raster(const Views &v, const RasterArgs &a, int attr, cudaStream_t s);
 void launch_count_large(const Views &v, const BinArgs &a, int sms, cudaStream_t s);
+// Slot offsets and cursors from counts + ovf (ovf is overwritten with the sums).
+void launch_slot_offsets(int m, int *counts, int *ovf, long long *offsets, long long *cursor,
+                         long long *total, cudaStream_t s);
+
 // Exclusive scan of in[0..m) into out[0..m] (out[m] = total); cursor (may be
 // null) receives a copy of out[0..m); seg_totals[k] = total of the k-th of
 // nseg equal segments.

@@ -186,10 +186,8 @@ __device__ __forceinline__ int foot_slot(const FrameConst &fc, const TileFoot &f
 // never emptied while a CTA runs, so that choice is the same for every
 // occurrence of the key within the CTA.
 // ---------------------------------------------------------------------------
-constexpr int kHashBits = 11;
-constexpr int kHash = 1 << kHashBits; // slots
+// kHashBits, kHash (slots) and kChunk (particles per CTA) are in spl_internal.cuh
 constexpr int kProbe = 32;
-constexpr int kChunk = 2048;         // particles per CTA in the binning kernels
 
 __device__ __forceinline__ int hash_slot(const int *keys, int key, bool insert) {
     unsigned h = ((unsigned)key * 2654435761u) >> (32 - kHashBits);
@@ -206,15 +204,16 @@ __device__ __forceinline__ int hash_slot(const int *keys, int key, bool insert) 
     return -1;
 }
 
-// Count the slots of one round (k-th tile of every lane's footprint).
-__device__ __forceinline__ void count_round(int key, int *keys, int *vals, int *gcounts, int lane) {
+// Count the slots of one round (k-th tile of every lane's footprint); a key
+// with no room in the table is counted in ovf (placed through the cursors).
+__device__ __forceinline__ void count_round(int key, int *keys, int *vals, int *govf, int lane) {
     const unsigned m = __match_any_sync(0xffffffffu, key);
     if (key >= 0 && lane == __ffs(m) - 1) {
         const int slot = hash_slot(keys, key, true);
         if (slot >= 0)
             atomicAdd(&vals[slot], __popc(m));
         else
-            atomicAdd(&gcounts[key], __popc(m));
+            atomicAdd(&govf[key], __popc(m));
     }
 }
 
@@ -225,11 +224,16 @@ __device__ __forceinline__ void hash_clear(int *keys, int *vals) {
     }
 }
 
-// Flush the CTA's hash table into the global slot counts and clear it.
-__device__ __forceinline__ void hash_flush(int *keys, int *vals, int *gcounts) {
+// Flush the CTA's hash table into the global slot counts, keep the table
+// with every slot's offset inside its slot (tab: kHash entries) for the
+// scatter, and clear it.
+__device__ __forceinline__ void hash_flush(int *keys, int *vals, int *gcounts, int2 *tab) {
     __syncthreads();
     for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
-        if (keys[k] >= 0) atomicAdd(&gcounts[keys[k]], vals[k]);
+        const int key = keys[k];
+        int off = 0;
+        if (key >= 0) off = atomicAdd(&gcounts[key], vals[k]);
+        tab[k] = make_int2(key, off);
         keys[k] = -1;
         vals[k] = 0;
     }
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
             const int maxk = __reduce_max_sync(0xffffffffu, foot.nbox);
             for (int k = 0; k < maxk; ++k) {
                 const int ls = foot_slot(fc, foot, k, r0, r1);
-                count_round(ls >= 0 ? fc.slot_base + ls : -1, keys, vals, a.counts, lane);
+                count_round(ls >= 0 ? fc.slot_base + ls : -1, keys, vals, a.ovf, lane);
             }
             n_act += cls != CLS_INACTIVE;
             n_pt += cls == CLS_POINT;
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
             }
         }
         // one global atomic per distinct slot of this CTA and view
-        hash_flush(keys, vals, a.counts);
+        hash_flush(keys, vals, a.counts, a.ctab + ((int64_t)blockIdx.x * vs.nviews + v) * kHash);
     }
     n_act = __reduce_add_sync(0xffffffffu, n_act);
     n_pt = __reduce_add_sync(0xffffffffu, n_pt);
@@ -363,7 +367,7 @@ __global__ void __launch_bounds__(256) large_tiles_kernel(Views vs, BinArgs a) {
             if (!disc_meets_tile(fc, r0, r1.x, tx, ty)) continue;
             const int slot = fc.slot_base + L_LARGE * fc.ntiles + ty * fc.ntx + tx;
             if (MODE == 0) {
-                atomicAdd(&a.counts[slot], 1);
+                atomicAdd(&a.ovf[slot], 1);
             } else {
                 const long long pos =
                     (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.cursor[slot]), 1ULL);
@@ -379,6 +383,17 @@ __global__ void __launch_bounds__(256) large_tiles_kernel(Views vs, BinArgs a) {
 void launch_count_large(const Views &vs, const BinArgs &a, int sms, cudaStream_t s) {
     if (vs.n <= 0) return;
     large_tiles_kernel<0><<<sms * 2, 256, 0, s>>>(vs, a);
+}
+
+__global__ void slot_sum_kernel(int m, const int *counts, int *ovf) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
+        ovf[k] += counts[k];
+}
+
+__global__ void slot_cursor_kernel(int m, const int *counts, const long long *offsets,
+                                   long long *cursor) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
+        cursor[k] = offsets[k] + counts[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -434,6 +449,14 @@ void launch_scan(int m, const int *in, long long *out, long long *cursor, int ns
 void launch_scan(int m, const int *in, int *out, int *cursor, int nseg, int *seg_totals,
                  cudaStream_t s) {
     scan_kernel<int><<<1, 1024, 0, s>>>(m, in, out, cursor, nseg, seg_totals);
+}
+
+void launch_slot_offsets(int m, int *counts, int *ovf, long long *offsets, long long *cursor,
+                         long long *total, cudaStream_t s) {
+    const int grid = (m + 255) / 256 < 1024 ? (m + 255) / 256 : 1024;
+    if (grid > 0) slot_sum_kernel<<<grid, 256, 0, s>>>(m, counts, ovf);
+    scan_kernel<long long><<<1, 1024, 0, s>>>(m, ovf, offsets, nullptr, 1, total);
+    if (grid > 0) slot_cursor_kernel<<<grid, 256, 0, s>>>(m, counts, offsets, cursor);
 }
 
 // ---------------------------------------------------------------------------
@@ -540,11 +563,13 @@ __device__ __forceinline__ TileFoot load_foot(const FrameConst &fc, const BinArg
 }
 
 // Scatter record indices of points, small and medium particles into their
-// tiles' lists.  Per CTA and view: count its chunk's slots in the shared hash
-// table, reserve one contiguous range per slot with one global atomic, then
-// place every entry at range base + local rank.  Order inside a tile follows
-// the atomics, which is harmless: E_p = A_p makes the sum order-independent
-// (Sec. 2).
+// tiles' lists in one pass: per CTA and view, the rasteriser's table gives
+// every slot the CTA used its range base offsets[slot] + offset; each entry
+// goes to base + its rank among the CTA's entries of that slot (shared-memory
+// counters, lanes of a warp with the same slot combined by a match mask).
+// Keys that had no room in the table go through the cursors.  Order inside a
+// tile follows the atomics, which is harmless: E_p = A_p makes the sum
+// order-independent (Sec. 2); the absorption mode sorts the lists afterwards.
 __global__ void __launch_bounds__(256) scatter_kernel(Views vs, BinArgs a) {
     extern __shared__ long long scatter_smem[];
     long long *bases = scatter_smem;                         // kHash
@@ -556,35 +581,16 @@ __global__ void __launch_bounds__(256) scatter_kernel(Views vs, BinArgs a) {
     const int64_t c0 = (int64_t)blockIdx.x * kChunk;
     const int64_t c1 = c0 + kChunk < vs.n ? c0 + kChunk : vs.n;
     for (int v = 0; v < vs.nviews; ++v) {
-        hash_clear(keys, vals);
-        load_view(vs.fcs, v, &sfc);
+        load_view(vs.fcs, v, &sfc);     // (begins and ends with a barrier)
         const FrameConst &fc = sfc;
-        // pass 1: local counts
-        for (int64_t base = c0; base < c1; base += blockDim.x) {
-            const int64_t i = base + threadIdx.x;
-            float4 r0, r1;
-            const TileFoot f = load_foot(fc, a, fc.rec_base + i, i < c1, r0, r1);
-            const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
-            for (int k = 0; k < maxk; ++k) {
-                const int ls = foot_slot(fc, f, k, r0, r1);
-                const int key = ls >= 0 ? fc.slot_base + ls : -1;
-                const unsigned m = __match_any_sync(0xffffffffu, key);
-                if (key >= 0 && lane == __ffs(m) - 1) {
-                    const int slot = hash_slot(keys, key, true);
-                    if (slot >= 0) atomicAdd(&vals[slot], __popc(m));
-                }
-            }
-        }
-        __syncthreads();
-        // reserve one range per slot
+        const int2 *tab = a.ctab + ((int64_t)blockIdx.x * vs.nviews + v) * kHash;
         for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
-            if (keys[k] >= 0)
-                bases[k] = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.cursor[keys[k]]),
-                                                (unsigned long long)vals[k]);
+            const int2 t = tab[k];
+            keys[k] = t.x;
             vals[k] = 0;
+            bases[k] = t.x >= 0 ? a.offsets[t.x] + t.y : 0;
         }
         __syncthreads();
-        // pass 2: place the entries
         for (int64_t base = c0; base < c1; base += blockDim.x) {
             const int64_t i = base + threadIdx.x;
             const int64_t rec = fc.rec_base + i;
@@ -614,7 +620,6 @@ __global__ void __launch_bounds__(256) scatter_kernel(Views vs, BinArgs a) {
                 }
             }
         }
-        __syncthreads();
     }
 }
 
