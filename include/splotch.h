@@ -115,8 +115,8 @@ typedef struct {
     double r_sml;              /* point rule for r <= r_sml (default 0.5) */
     double brightness;         /* emission scale (default 1) */
     int32_t tile_px;           /* tile side t_x = t_y of Eq. 8: 16, 32 or 64 (default 32) */
-    double r_small;            /* r_sml < r <= r_small: one warp per particle over its pixel box
-                                * (default 0.5 = r_sml: no such class, the tile pass takes them) */
+    double r_small;            /* r_sml < r <= r_small: one thread per particle over its pixel box
+                                * (default 2; r_small = r_sml: no such class) */
     double r_large;            /* r > r_large: large pass (default 64) */
     int32_t mode;              /* SPL_MODE_ADDITIVE, SPL_MODE_EA or SPL_MODE_ABSORB */
     int32_t sched;             /* SPL_SCHED_* (default SPL_SCHED_NONE) */
@@ -206,8 +206,8 @@ int spl_render_batch(spl_ctx *ctx, const spl_camera *cams, int32_t n_views,
 
 /* Autotuner (the empirical tuning of tile size and chunking of Sec. 5.1,
  * done by timing): renders the batch with every candidate tile side
- * (16, 32, 64) and class-radius pair (r_small, r_large) in {(r_sml, 32),
- * (r_sml, 64), (r_sml, 128), (r_sml, inf), (2, 64)}, reps timed renders each, keeps the fastest as the
+ * (16, 32, 64) and class-radius pair (r_small, r_large) in {(2, 32), (2, 64),
+ * (2, 128), (2, inf), (3, 64), (r_sml, 64)}, reps timed renders each, keeps the fastest as the
  * context's parameters and returns it in *best (and its time per batch in
  * *best_ms; either may be NULL).  The images are overwritten. */
 int spl_autotune(spl_ctx *ctx, const spl_camera *cams, int32_t n_views, float *const *d_images,

@@ -165,7 +165,7 @@ extern "C" int spl_default_params(spl_params *q) {
     q->r_sml = 0.5;
     q->brightness = 1.0;
     q->tile_px = 32;
-    q->r_small = 0.5;
+    q->r_small = 2.0;
     q->r_large = 64.0;
     q->mode = SPL_MODE_ADDITIVE;
     q->sched = SPL_SCHED_NONE;
@@ -960,7 +960,7 @@ extern "C" int spl_autotune(spl_ctx *c, const spl_camera *cams, int32_t n_views,
     if (c->par.mode == SPL_MODE_ABSORB) return SPL_EINVAL;   // single views only
     DeviceGuard g(c->device);
     static const int tiles[] = {16, 32, 64};
-    static const double radii[][2] = {{0.0, 32.0}, {0.0, 64.0}, {0.0, 128.0}, {0.0, 1e9}, {2.0, 64.0}};
+    static const double radii[][2] = {{2.0, 32.0}, {2.0, 64.0}, {2.0, 128.0}, {2.0, 1e9}, {3.0, 64.0}, {0.0, 64.0}};
     const spl_params base = c->par;
     spl_params bp = base;
     float bms = -1.f;

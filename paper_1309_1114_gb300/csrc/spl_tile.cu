@@ -15,8 +15,8 @@
 //   - point particles (r <= r_sml, Sec. 4.1) add their emission to one pixel
 //     of a shared-memory copy of the tile; lanes of a warp that hit the same
 //     pixel are summed with warp shuffles first;
-//   - small particles (r_sml < r <= r_small): one warp per particle spreads
-//     the particle's pixel box over its lanes, into shared memory;
+//   - small particles (r_sml < r <= r_small, a few pixels wide): one thread
+//     per particle walks the particle's pixel box, into shared memory;
 //   - medium and large particles are taken in batches (the chunks of n_p
 //     particles of Sec. 4.2): the CTA first tabulates, per particle, the
 //     column weights w_x(i) = exp(-dx^2/sigma^2) and the row terms
@@ -108,33 +108,32 @@ struct Acc<T, true> {
     }
 };
 
-// One small particle into the shared tile: the warp spreads the particle's
-// pixel box (inside the tile) over its lanes, so no two lanes of a warp touch
-// the same pixel; different warps meet only through shared-memory atomics.
+// One small particle (a few pixels wide) into the shared tile, by one thread:
+// the pixel box inside the tile, the clip test and the weight of Eq. 2 per
+// pixel, and one shared-memory add per channel.  A tiny splat costs a few
+// pixels of work here instead of a batch-table share and a band visit.
 template <int T>
-__device__ __forceinline__ void warp_small(const FrameConst &fc, float4 r0, float4 r1, int x0,
-                                           int y0, float (*sacc)[T][T], int lane) {
+__device__ __forceinline__ void thread_small(const FrameConst &fc, float4 r0, float4 r1, int x0,
+                                             int y0, float (*sacc)[T][T]) {
     PixBox b;
     if (!splat_box(fc, r0, r1.x, b)) return;
     const int i0 = max(b.i0, x0), i1 = min(b.i1, x0 + T - 1);
     const int j0 = max(b.j0, y0), j1 = min(b.j1, y0 + T - 1);
-    if (i0 > i1 || j0 > j1) return;
     const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
     const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
     const float kq = r0.w, r2 = r1.x;
-    const int bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
-    const float inv_bw = 1.f / (float)bw;
-    for (int q = lane; q < npx; q += 32) {
-        int jj = (int)(((float)q + 0.5f) * inv_bw);
-        int ii = q - jj * bw;
-        const int i = i0 + ii, j = j0 + jj;
-        const float dx = (float)(i - xi) + xh, dy = (float)(j - yi) + yh;
-        const float d2 = dx * dx + dy * dy;
-        if (d2 <= r2) {
-            const float w = ex2_neg(kq * d2);
-            atomicAdd(&sacc[0][j - y0][i - x0], r1.y * w);
-            atomicAdd(&sacc[1][j - y0][i - x0], r1.z * w);
-            atomicAdd(&sacc[2][j - y0][i - x0], r1.w * w);
+    for (int j = j0; j <= j1; ++j) {
+        const float dy = (float)(j - yi) + yh;
+        const float rem = r2 - dy * dy;
+        for (int i = i0; i <= i1; ++i) {
+            const float dx = (float)(i - xi) + xh;
+            const float dx2 = dx * dx;
+            if (dx2 <= rem) {
+                const float w = ex2_neg(kq * (dx2 + dy * dy));
+                atomicAdd(&sacc[0][j - y0][i - x0], r1.y * w);
+                atomicAdd(&sacc[1][j - y0][i - x0], r1.z * w);
+                atomicAdd(&sacc[2][j - y0][i - x0], r1.w * w);
+            }
         }
     }
 }
@@ -427,19 +426,13 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
             warp_points<T>(a, st0 + warp * 32, st1 + warp * 32, cnt - warp * 32, x0, y0, sacc, lane);
             __syncthreads();
         }
-        // small particles: one warp each over the pixel box
+        // small particles: one thread each over its pixel box (no staging)
 #pragma unroll 1
-        for (long long base = lb1; base < le1; base += kTileThreads) {
-            const int cnt = (int)(le1 - base < kTileThreads ? le1 - base : kTileThreads);
-            if (tid < cnt) {
-                const unsigned id = a.entries[base + tid];
-                st0[tid] = a.rec0[id];
-                st1[tid] = a.rec1[id];
-            }
-            __syncthreads();
-            for (int k = warp; k < cnt; k += NW) warp_small<T>(fc, st0[k], st1[k], x0, y0, sacc, lane);
-            __syncthreads();
+        for (long long k = lb1 + tid; k < le1; k += kTileThreads) {
+            const unsigned id = a.entries[k];
+            thread_small<T>(fc, a.rec0[id], a.rec1[id], x0, y0, sacc);
         }
+        if (le1 > lb1) __syncthreads();
         // write: shared part + registers, stored (only item of its tile; added
         // to the previous chunks' sum when accumulating) or added atomically
         const bool store = !LARGE && list < 0;
