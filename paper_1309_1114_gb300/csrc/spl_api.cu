@@ -616,12 +616,15 @@ static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
     ta.accumulate = c->accumulate ? 1 : 0;
     // scheduling: per-item features, predicted cost, longest first
     const bool sched = c->par.sched != SPL_SCHED_NONE;
-    // exact features when recording training samples, else a 64-entry sample
-    if (sched || c->recording)
+    const float *theta = c->par.sched == SPL_SCHED_MLP && c->have_model ? c->theta.p : nullptr;
+    // exact features when recording training samples, else a 64-entry sample;
+    // the count heuristic needs only the entry counts
+    if (c->recording || theta)
         launch_item_features(vs, ta, (float)vs.tile * (float)vs.tile, c->recording ? 0 : 64,
                              c->feat.p, c->item_n.p, c->sms, s);
+    else if (sched)
+        launch_item_entries(vs, ta, c->item_n.p, c->sms, s);
     if (sched) {
-        const float *theta = c->par.sched == SPL_SCHED_MLP && c->have_model ? c->theta.p : nullptr;
         launch_item_cost(c->feat.p, c->item_n.p, theta, c->heur.p, ta.items_cap, c->dstats.p,
                          c->cost.p, s);
         launch_order_items(c->cost.p, ta.items_cap, c->dstats.p, c->order_hist.p, c->order.p, s);

@@ -205,6 +205,8 @@ void launch_count_work(const FrameConst &fc, const float4 *rec0, const float4 *r
 
 // Scheduling of the work items (spl_sched.cu): per-item features, predicted
 // cost (network or count heuristic), and a longest-first order per pass.
+void launch_item_entries(const Views &v, const TileArgs &a, int *n_entries, int sms,
+                         cudaStream_t s);
 void launch_item_features(const Views &v, const TileArgs &a, float area_scale, int max_sample,
                           float *feat, int *n_entries, int sms, cudaStream_t s);
 void launch_item_cost(const float *feat, const int *n_entries, const float *theta,

@@ -98,6 +98,30 @@ void launch_item_features(const Views &vs, const TileArgs &a, float area_scale, 
     item_features_kernel<<<sms * 4, 256, 0, s>>>(vs, a, area_scale, max_sample, feat, n_entries);
 }
 
+// Entries of every item only (what the count heuristic needs): a segment's
+// length, or the sum of a whole tile's list lengths.
+__global__ void item_entries_kernel(Views vs, TileArgs a, int *n_entries) {
+    const int n_all = min(a.st->item_totals[0] + a.st->item_totals[1], a.items_cap);
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n_all; it += gridDim.x * blockDim.x) {
+        const WorkItem w = a.items[it];
+        long long cnt = w.end - w.start;
+        if (item_list(w) < 0) {
+            const FrameConst &fc = vs.fcs[item_view(w)];
+            const int tile = w.tile - fc.tile_base;
+            cnt = 0;
+            for (int l = 0; l < 3; ++l)
+                cnt += a.offsets[fc.slot_base + l * fc.ntiles + tile + 1] -
+                       a.offsets[fc.slot_base + l * fc.ntiles + tile];
+        }
+        n_entries[it] = (int)cnt;
+    }
+}
+
+void launch_item_entries(const Views &vs, const TileArgs &a, int *n_entries, int sms,
+                         cudaStream_t s) {
+    item_entries_kernel<<<sms * 4, 256, 0, s>>>(vs, a, n_entries);
+}
+
 // Predicted log-cycles of every item: the network when theta is given, else
 // the count heuristic heur[0] + heur[1] log1p(entries).
 __global__ void __launch_bounds__(256) item_cost_kernel(const float *feat, const int *n_entries,
