@@ -55,6 +55,9 @@ struct Shape {
     static constexpr int P = 32;                   // particles per tabulated batch
     static constexpr int PER = T / 8;              // table columns (and rows) per thread
     static constexpr bool PAIRED = RPL % 2 == 0;   // rows two at a time (FP32x2)
+    // row stride of the column table: 8 entries of padding put the two
+    // particles that a half-warp's 64-bit stores reach in different banks
+    static constexpr int WXS = T + 8;
 };
 
 // Two FP32 values in one 64-bit register pair: the operand of the packed
@@ -180,16 +183,17 @@ __device__ __forceinline__ void warp_points(const TileArgs &a, const float4 *s0,
 // swx[p][c] = (w_x, dx^2 B) for tile column c; for tile row j the row terms
 // e_R w_y, e_G w_y, e_B w_y and (r^2 - dy^2) B + 1.  Rows are stored one
 // float4 per row, or -- when the rows go two at a time -- per row pair
-// (2m, 2m+1) as srow[p][2m] = (e_R w_y, same for row 2m+1, e_G w_y, e_G w_y')
-// and srow[p][2m+1] = (e_B w_y, e_B w_y', rem, rem'), so that every packed
-// operand is one aligned half of a 16-byte load.  Thread (p, q) = (tid / 8,
+// (2m, 2m+1) in two tables, srow[p][m] = (e_R w_y, same for row 2m+1, e_G w_y,
+// e_G w_y') in the first half of the row space and (e_B w_y, e_B w_y', rem,
+// rem') in the second, so that every packed operand is one aligned half of a
+// 16-byte load and the eight threads of a particle store consecutive entries.  Thread (p, q) = (tid / 8,
 // tid % 8) fills columns q, q + 8, q + 16, ... (and the same rows, or row
 // pairs q, q + 8, ...) of particle p.  It also decides for row band q whether
 // the disc reaches it (bit p of band_mask[q]).  B only needs to be the same
 // on both sides of the clip test, so a fast reciprocal serves.
 template <int T>
 __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, int cnt, int x0,
-                                         int y0, float2 (*swx)[T], float4 (*srow)[T],
+                                         int y0, float2 (*swx)[Shape<T>::WXS], float4 (*srow)[T],
                                          unsigned *band_mask, int tid) {
     using S = Shape<T>;
     const int p = tid >> 3, q = tid & 7;
@@ -219,8 +223,9 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
             const float dya = (float)(y0 + 2 * m - yi) + yh, dyb = (float)(y0 + 2 * m + 1 - yi) + yh;
             const float a2 = dya * dya, b2 = dyb * dyb;
             const float wa = ex2_neg(kq * a2), wb = ex2_neg(kq * b2);
-            srow[p][2 * m] = make_float4(r1.y * wa, r1.y * wb, r1.z * wa, r1.z * wb);
-            srow[p][2 * m + 1] =
+            float4 *rowA = reinterpret_cast<float4 *>(srow), *rowB = rowA + S::P * (T / 2);
+            rowA[p * (T / 2) + m] = make_float4(r1.y * wa, r1.y * wb, r1.z * wa, r1.z * wb);
+            rowB[p * (T / 2) + m] =
                 make_float4(r1.w * wa, r1.w * wb, fmaf(r2 - a2, B, 1.f), fmaf(r2 - b2, B, 1.f));
         }
     } else {
@@ -267,6 +272,7 @@ __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp
 
 // The same two rows at a time: per row pair two 16-byte loads, two scalar
 // clips, one packed multiply and three packed FMAs (R, G, B of both rows).
+// rowp points at the particle's first-half row-pair table (see tabulate).
 template <int T>
 __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp, int col, int row0,
                                            Acc<T, true> &acc) {
@@ -279,10 +285,11 @@ __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp
         ww[k] = pack2(v.x, v.x);
         dxb[k] = v.y;
     }
-    const ulonglong2 *rp = reinterpret_cast<const ulonglong2 *>(rowp) + row0;
+    const ulonglong2 *ra_ = reinterpret_cast<const ulonglong2 *>(rowp) + row0 / 2;
+    const ulonglong2 *rb_ = ra_ + S::P * (T / 2);
 #pragma unroll
     for (int m = 0; m < S::RPL / 2; ++m) {
-        const ulonglong2 a = rp[2 * m], b = rp[2 * m + 1];
+        const ulonglong2 a = ra_[m], b = rb_[m];
         float ra, rb;
         unpack2(b.y, ra, rb);
 #pragma unroll
@@ -302,7 +309,7 @@ __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp
 template <int T>
 __host__ __device__ constexpr size_t table_bytes() {
     using S = Shape<T>;
-    return (sizeof(float4) + sizeof(float2)) * S::P * T;
+    return sizeof(float4) * S::P * T + sizeof(float2) * S::P * S::WXS;
 }
 static_assert(table_bytes<16>() >= sizeof(float) * 3 * 16 * 16, "shared tile fits the tables");
 static_assert(table_bytes<32>() >= sizeof(float) * 3 * 32 * 32, "shared tile fits the tables");
@@ -322,7 +329,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
     constexpr int NW = kTileThreads / 32;
     extern __shared__ float4 smem_raw[];
     float4 (*srow)[T] = reinterpret_cast<float4 (*)[T]>(smem_raw);
-    float2 (*swx)[T] = reinterpret_cast<float2 (*)[T]>(smem_raw + S::P * T);
+    float2 (*swx)[S::WXS] = reinterpret_cast<float2 (*)[S::WXS]>(smem_raw + S::P * T);
     float (*sacc)[T][T] = reinterpret_cast<float (*)[T][T]>(smem_raw);   // after the tables
     float4 *st0 = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + table_bytes<T>());
     float4 *st1 = st0 + kTileThreads;
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
             while (mask) {
                 const int p = __ffs(mask) - 1;
                 mask &= mask - 1u;
-                band_splat<T>(swx[p], srow[p], col, row0, acc);
+                band_splat<T>(swx[p], S::PAIRED ? srow[0] + p * (T / 2) : srow[p], col, row0, acc);
             }
             __syncthreads();
         }
