@@ -209,18 +209,22 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
     const int ihi = xi - x0 + (int)floorf(fminf(r0.y - 0.5f + r, 1e6f));
     const int jlo = yi - y0 + (int)ceilf(fmaxf(r0.z - 0.5f - r, -1e6f));
     const int jhi = yi - y0 + (int)floorf(fminf(r0.z - 0.5f + r, 1e6f));
+    // offsets of this thread's first column and row from the particle centre;
+    // the others follow by adding small integers (exact in FP32)
+    const float dxq = ((float)(x0 - xi) + xh) + (float)q;
 #pragma unroll
     for (int u = 0; u < S::PER; ++u) {
         const int k = q + 8 * u;
-        const float dx = (float)(x0 + k - xi) + xh;
+        const float dx = dxq + (float)(8 * u);
         const float dx2 = dx * dx;
         swx[p][k] = make_float2(ex2_neg(kq * dx2), dx2 * B);
     }
     if constexpr (S::PAIRED) {
+        const float dyq = ((float)(y0 - yi) + yh) + (float)(2 * q);
 #pragma unroll
         for (int u = 0; u < S::PER / 2; ++u) {
             const int m = q + 8 * u;
-            const float dya = (float)(y0 + 2 * m - yi) + yh, dyb = (float)(y0 + 2 * m + 1 - yi) + yh;
+            const float dya = dyq + (float)(16 * u), dyb = dya + 1.f;
             const float a2 = dya * dya, b2 = dyb * dyb;
             const float wa = ex2_neg(kq * a2), wb = ex2_neg(kq * b2);
             float4 *rowA = reinterpret_cast<float4 *>(srow), *rowB = rowA + S::P * (T / 2);
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
     float (*sacc)[T][T] = reinterpret_cast<float (*)[T][T]>(smem_raw);   // after the tables
     float4 *st0 = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem_raw) + table_bytes<T>());
     float4 *st1 = st0 + kTileThreads;
-    __shared__ unsigned band_mask[NW];
+    __shared__ unsigned band_mask[2][NW];
     __shared__ int s_item;
     __shared__ FrameConst sfc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -378,38 +382,53 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
         acc.zero();
 
         // medium (or large) particles: tabulate a batch, then every row band
-        // adds it; the next batch's records are fetched into registers while
-        // the current one is processed
+        // adds it.  Records are staged in two alternating buffers (with two
+        // band-mask sets): the next batch is stored while the bands of this one
+        // are added, and the batch after it is fetched into registers.
         float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
-        if (lb2 + tid < le2 && tid < S::P) {
-            const unsigned id = a.entries[lb2 + tid];
-            n0 = a.rec0[id];
-            n1 = a.rec1[id];
-        }
-#pragma unroll 1
-        for (long long base = lb2; base < le2; base += S::P) {
-            const int cnt = (int)(le2 - base < S::P ? le2 - base : S::P);
-            if (tid < cnt) {
-                st0[tid] = n0;
-                st1[tid] = n1;
+        if (lb2 < le2) {
+            if (lb2 + tid < le2 && tid < S::P) {
+                const unsigned id = a.entries[lb2 + tid];
+                st0[tid] = a.rec0[id];
+                st1[tid] = a.rec1[id];
             }
-            if (tid < NW) band_mask[tid] = 0u;
-            __syncthreads();
-            if (base + S::P + tid < le2 && tid < S::P) {
-                const unsigned id = a.entries[base + S::P + tid];
+            if (tid < NW) band_mask[0][tid] = 0u;
+            if (lb2 + S::P + tid < le2 && tid < S::P) {
+                const unsigned id = a.entries[lb2 + S::P + tid];
                 n0 = a.rec0[id];
                 n1 = a.rec1[id];
             }
-            tabulate<T>(st0, st1, cnt, x0, y0, swx, srow, band_mask, tid);
             __syncthreads();
+        }
+        int buf = 0;
+#pragma unroll 1
+        for (long long base = lb2; base < le2; base += S::P) {
+            const int cnt = (int)(le2 - base < S::P ? le2 - base : S::P);
+            tabulate<T>(st0 + buf * S::P, st1 + buf * S::P, cnt, x0, y0, swx, srow, band_mask[buf],
+                        tid);
+            __syncthreads();
+            // stage the next batch (its buffer and masks were last used a batch ago)
+            if (tid < S::P) {
+                if (base + S::P + tid < le2) {
+                    st0[(buf ^ 1) * S::P + tid] = n0;
+                    st1[(buf ^ 1) * S::P + tid] = n1;
+                }
+                if (base + 2 * S::P + tid < le2) {
+                    const unsigned id = a.entries[base + 2 * S::P + tid];
+                    n0 = a.rec0[id];
+                    n1 = a.rec1[id];
+                }
+            }
+            if (tid < NW) band_mask[buf ^ 1][tid] = 0u;
             // this warp's row band: only the particles that reach it
-            unsigned mask = band_mask[warp];
+            unsigned mask = band_mask[buf][warp];
             while (mask) {
                 const int p = __ffs(mask) - 1;
                 mask &= mask - 1u;
                 band_splat<T>(swx[p], S::PAIRED ? srow[0] + p * (T / 2) : srow[p], col, row0, acc);
             }
             __syncthreads();
+            buf ^= 1;
         }
 
         // points and small particles go through the shared tile, which reuses
