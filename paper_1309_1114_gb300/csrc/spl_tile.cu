@@ -242,10 +242,15 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
             srow[p][k] = make_float4(r1.y * wy, r1.z * wy, r1.w * wy, fmaf(r2 - dy2, B, 1.f));
         }
     }
-    // row band q: columns [bx BW, bx BW + BW), rows [by BH, by BH + BH)
+    // row band q: columns [bx BW, bx BW + BW), rows [by BH, by BH + BH); the
+    // disc (with the box's margin) must reach the band's nearest pixel centre
     const int bx0 = (q % S::NBX) * S::BW, by0 = (q / S::NBX) * S::BH;
     const int bx1 = bx0 + S::BW - 1, by1 = by0 + S::BH - 1;
-    if (jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1) atomicOr(&band_mask[q], 1u << p);
+    const float ax = (float)(x0 + bx0 - xi) + xh, ay = (float)(y0 + by0 - yi) + yh;
+    const float nx = fmaxf(ax, fminf(0.f, ax + (float)(S::BW - 1)));
+    const float ny = fmaxf(ay, fminf(0.f, ay + (float)(S::BH - 1)));
+    if (jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1 && nx * nx + ny * ny <= r * r)
+        atomicOr(&band_mask[q], 1u << p);
 }
 
 // Add tabulated particle p into the registers of this thread's pixels.  The
