@@ -197,8 +197,10 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
                                          unsigned *band_mask, int tid) {
     using S = Shape<T>;
     const int p = tid >> 3, q = tid & 7;
-    if (p >= cnt) return;
-    const float4 r0 = st0[p], r1 = st1[p];
+    // every lane runs to the end (the band bits are combined by a ballot); the
+    // entries of particles p >= cnt are written but never read (no band bit)
+    const bool valid = p < cnt;
+    const float4 r0 = st0[valid ? p : 0], r1 = st1[valid ? p : 0];
     const float kq = r0.w, r2 = r1.x;
     const float B = __fdividef(1048576.f, r2);
     const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
@@ -249,8 +251,17 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
     const float ax = (float)(x0 + bx0 - xi) + xh, ay = (float)(y0 + by0 - yi) + yh;
     const float nx = fmaxf(ax, fminf(0.f, ax + (float)(S::BW - 1)));
     const float ny = fmaxf(ay, fminf(0.f, ay + (float)(S::BH - 1)));
-    if (jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1 && nx * nx + ny * ny <= r * r)
-        atomicOr(&band_mask[q], 1u << p);
+    const bool hit = valid && jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1 &&
+                     nx * nx + ny * ny <= r * r;
+    // lane 8j + q holds particle 4w + j of warp w and band q: lane q < 8 gathers
+    // its band's four bits and sets them with one atomic
+    const unsigned hb = __ballot_sync(0xffffffffu, hit);
+    const int lane = tid & 31;
+    if (lane < 8) {
+        const unsigned nib = ((hb >> lane) & 1u) | (((hb >> (lane + 8)) & 1u) << 1) |
+                             (((hb >> (lane + 16)) & 1u) << 2) | (((hb >> (lane + 24)) & 1u) << 3);
+        if (nib) atomicOr(&band_mask[lane], nib << (4 * (tid >> 5)));
+    }
 }
 
 // Add tabulated particle p into the registers of this thread's pixels.  The
