@@ -16,6 +16,10 @@ the header comment of ``splotch_oracle.c``.  Parity status per function:
   ``tests/test_oracle_mlp.py``.
 * ``tile_features``: pinned by hand-counted cases in
   ``tests/test_oracle_pins.py``.
+* colouring options (per-particle components ``cr``, ``cg``, ``cb`` in the
+  particle dict; ``par["log"]`` bit 1 = log10 of I, bit 2 = log10 of s):
+  pinned by a hand value, the constant-palette equivalence, channel
+  separation and exact powers of ten in ``tests/test_oracle_colour.py``.
 * ``render`` / ``render_bruteforce`` with ``mode = 2`` (Eq. 1 with independent
   emission and absorption over depth-ordered particles): pinned by hand-worked
   two-particle cases (both orders, equal depths), the E = A special case, the
@@ -48,7 +52,9 @@ class _Params(C.Structure):
     _fields_ = [("chi", C.c_double), ("sigma_per_h", C.c_double),
                 ("s_box", C.c_double), ("r_sml", C.c_double),
                 ("brightness", C.c_double), ("s_min", C.c_double),
-                ("s_max", C.c_double), ("mode", C.c_int), ("absorption", C.c_double)]
+                ("s_max", C.c_double), ("mode", C.c_int), ("absorption", C.c_double),
+                ("log_flags", C.c_int), ("cr", C.c_void_p), ("cg", C.c_void_p),
+                ("cb", C.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -118,6 +124,7 @@ def _params(par: dict | None) -> _Params:
     q.s_max = float(par.get("s_max", 1.0))
     q.mode = int(par.get("mode", 0))
     q.absorption = float(par.get("absorption", 1.0))
+    q.log_flags = int(par.get("log", 0))
     return q
 
 
@@ -132,7 +139,14 @@ def _args(parts: dict, palette, cam, par):
     if pal.size % 3 or pal.size == 0:
         raise ValueError("palette must hold n*3 floats")
     c, q = _camera(cam), _params(par)
-    keep = (arrs, pal, c, q)
+    rgb = None
+    if "cr" in parts:
+        # per-particle colour components replace the palette (Sec. 2)
+        rgb = [_f32(parts[k]) for k in ("cr", "cg", "cb")]
+        if any(a.shape != (n,) for a in rgb):
+            raise ValueError("colour components must be 1-D and of the particle count")
+        q.cr, q.cg, q.cb = (a.ctypes.data for a in rgb)
+    keep = (arrs, pal, c, q, rgb)
     args = [n] + [_ptr(a, C.c_float) for a in arrs] + [_ptr(pal, C.c_float), pal.size // 3,
                                                        C.byref(c), C.byref(q)]
     return n, keep, args

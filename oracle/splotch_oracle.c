@@ -46,7 +46,13 @@
  *     k = min(floor(u), n-2), colour = pal[k] + (u-k)(pal[k+1]-pal[k]);
  *     emission e = brightness * I * colour (I plays rho0 of Eq. 2);
  *   - point rule weight 1 at pixel (floor(x_s), floor(y_s));
- *   - the clip is inclusive: d^2 <= r^2.
+ *   - the clip is inclusive: d^2 <= r^2;
+ *   - colour components (Sec. 2: a vector quantity such as a velocity gives
+ *     the R, G and B components directly): when per-particle components are
+ *     given they replace the palette, e = brightness * I * (c_R, c_G, c_B);
+ *   - logarithms of processed quantities (Sec. 2): optionally I is replaced by
+ *     log10(I), and s by log10(s) before its normalisation (s_min, s_max are
+ *     then in log units); a non-positive value makes the particle inactive.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -71,6 +77,8 @@ typedef struct {
     double s_min, s_max; /* colour-scalar normalisation (Sec. 4 footnote) */
     int mode;            /* 0: additive sum, 1: E=A map 1-exp(-S), 2: absorption */
     double absorption;   /* mode 2: A_p = absorption * brightness * I_p (> 0) */
+    int log_flags;       /* 1: log10 of I, 2: log10 of s (before normalisation) */
+    const float *cr, *cg, *cb;   /* per-particle colour components, or NULL (palette) */
 } orc_params;
 
 /* Class labels written by orc_project. */
@@ -156,7 +164,7 @@ static void palette(const float *pal, int npal, const orc_params *q, double s,
 
 /* Rasterisation of one particle (Sec. 2; Eq. 7; Sec. 4 classes). */
 static void project_one(const orc_view *v, const orc_params *q, const float *pal,
-                        int npal, double x, double y, double z, double hh,
+                        int npal, long p, double x, double y, double z, double hh,
                         double inten, double sc, orc_rec *o) {
     double d[3] = {x - v->eye[0], y - v->eye[1], z - v->eye[2]};
     double xc = dot3(v->right, d), yc = dot3(v->upc, d), zc = dot3(v->fwd, d);
@@ -169,12 +177,26 @@ static void project_one(const orc_view *v, const orc_params *q, const float *pal
     if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(hh) || !isfinite(inten) ||
         !isfinite(sc) || hh < 0.0)
         return;
+    if (q->cr && (!isfinite(q->cr[p]) || !isfinite(q->cg[p]) || !isfinite(q->cb[p]))) return;
     if (!(zc > v->z_near)) return;
+    if (q->log_flags & 1) {
+        if (!(inten > 0.0)) return;
+        inten = log10(inten);
+        o->ib = q->brightness * inten;
+    }
+    if (q->log_flags & 2) {
+        if (!(sc > 0.0)) return;
+        sc = log10(sc);
+    }
     o->xs = v->half_w + v->f * xc / zc;
     o->ys = v->half_h - v->f * yc / zc;
     o->sigma = q->sigma_per_h * hh * v->f / (zc * q->s_box);
     o->r = q->chi * o->sigma;
-    palette(pal, npal, q, sc, col);
+    if (q->cr) {
+        col[0] = q->cr[p]; col[1] = q->cg[p]; col[2] = q->cb[p];
+    } else {
+        palette(pal, npal, q, sc, col);
+    }
     for (int k = 0; k < 3; ++k) o->e[k] = q->brightness * inten * col[k];
     if (o->xs + o->r < 0.0 || o->xs - o->r >= v->w || o->ys + o->r < 0.0 ||
         o->ys - o->r >= v->h)
@@ -243,7 +265,7 @@ int orc_project(long n, const float *x, const float *y, const float *z,
     if (npal < 1 || make_view(cam, &v)) return -1;
     for (long p = 0; p < n; ++p) {
         orc_rec o;
-        project_one(&v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
+        project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
         xs[p] = o.xs; ys[p] = o.ys; sigma[p] = o.sigma; r[p] = o.r;
         for (int k = 0; k < 3; ++k) e[3 * p + k] = o.e[k];
         cls[p] = o.cls;
@@ -289,7 +311,7 @@ int orc_render(long n, const float *x, const float *y, const float *z,
             long lo = n * t / tn, hi = n * (t + 1) / tn;
             for (long p = lo; p < hi; ++p) {
                 orc_rec o;
-                project_one(&v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p],
+                project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p],
                             s[p], &o);
                 splat_one(&v, &o, part[t]);
             }
@@ -305,7 +327,7 @@ int orc_render(long n, const float *x, const float *y, const float *z,
 #endif
     for (long p = 0; p < n; ++p) {
         orc_rec o;
-        project_one(&v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
+        project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
         splat_one(&v, &o, img);
     }
     finish(q, img, npx);
@@ -368,7 +390,7 @@ int orc_render_pixels(long n, const float *x, const float *y, const float *z,
             for (long c = 0; c < nchunks; ++c) {
                 long lo = c * chunk, hi = lo + chunk < n ? lo + chunk : n;
                 for (long p = lo; p < hi; ++p)
-                    project_one(&v, q, pal, npal, x[p], y[p], z[p], h[p],
+                    project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p],
                                 inten[p], s[p], &rec[p - lo]);
                 for (long k = 0; k < npix; ++k) {
                     double *acc = part + ((long)t * npix + k) * 3;
@@ -400,7 +422,7 @@ int orc_render_bruteforce(long n, const float *x, const float *y, const float *z
     orc_rec *rec = (orc_rec *)malloc(sizeof(orc_rec) * (n > 0 ? n : 1));
     if (!rec) return -2;
     for (long p = 0; p < n; ++p)
-        project_one(&v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p], s[p], &rec[p]);
+        project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &rec[p]);
     for (long j = 0; j < v.h; ++j)
         for (long i = 0; i < v.w; ++i) {
             double acc[3] = {0.0, 0.0, 0.0};
@@ -427,7 +449,8 @@ int orc_render_bruteforce(long n, const float *x, const float *y, const float *z
  *     colour(s_p); absorption is grey, A_p = absorption * brightness * I_p
  *     (absorption > 0), so the source term E_p / A_p = colour(s_p) /
  *     absorption varies between particles and the order matters;
- *   - a particle with A_p = 0 (I_p = 0) emits nothing and absorbs nothing;
+ *   - a particle with A_p <= 0 (I_p = 0, or a non-positive logarithm of I)
+ *     emits nothing and absorbs nothing;
  *   - the ray starts with I = 0 behind the farthest particle and ends at the
  *     observer: particles are taken in decreasing camera depth, the depth key
  *     being z_c rounded to float, equal keys in decreasing particle index (so
@@ -485,8 +508,8 @@ static int render_absorb(long n, const float *x, const float *y, const float *z,
     }
     long m = 0;
     for (long p = 0; p < n; ++p) {
-        project_one(v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p], s[p], &rec[p]);
-        if (rec[p].cls != ORC_INACTIVE && q->absorption * rec[p].ib != 0.0) {
+        project_one(v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &rec[p]);
+        if (rec[p].cls != ORC_INACTIVE && q->absorption * rec[p].ib > 0.0) {
             ord[m].key = (float)rec[p].zc;
             ord[m].id = p;
             ++m;
@@ -607,7 +630,7 @@ int orc_ambiguity(long n, const float *x, const float *y, const float *z,
     long cnt = 0;
     for (long p = 0; p < n; ++p) {
         orc_rec o;
-        project_one(&v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
+        project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
         if (o.cls == ORC_INACTIVE) continue;
         if (q->mode == 2)
             for (int k = 0; k < 3; ++k) o.e[k] = fabs(o.ib) * pal_max;
@@ -727,7 +750,7 @@ int orc_tile_features(long n, const float *x, const float *y, const float *z,
     }
     for (long p = 0; p < n; ++p) {
         orc_rec o;
-        project_one(&v, q, pal, npal, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
+        project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &o);
         if (o.cls == ORC_INACTIVE) continue;
         int b = 0;
         if (o.r >= 1.0) {
