@@ -88,7 +88,12 @@ typedef struct {
     const void *h, *I, *s;     /* smoothing length, intensity, colour scalar:
                                   float or binary16 according to attr_type */
     int32_t attr_type;         /* SPL_ATTR_F32, SPL_ATTR_F16 or SPL_ATTR_F16_IS */
-    int32_t mem_space;         /* SPL_MEM_HOST or SPL_MEM_DEVICE (all six) */
+    int32_t mem_space;         /* SPL_MEM_HOST or SPL_MEM_DEVICE (all arrays) */
+    const float *cr, *cg, *cb; /* optional colour components (FP32, n each, all three or none):
+                                  they replace the palette look-up, e = brightness * I * (c_R,
+                                  c_G, c_B) -- the vector quantities of Sec. 2 (e.g. a velocity
+                                  gives R, G, B); a non-finite component makes the particle
+                                  inactive */
 } spl_particles;
 
 /* Pinhole camera (Sec. 2 "roto-translated and projected according to camera
@@ -121,7 +126,15 @@ typedef struct {
     int32_t mode;              /* SPL_MODE_ADDITIVE, SPL_MODE_EA or SPL_MODE_ABSORB */
     int32_t sched;             /* SPL_SCHED_* (default SPL_SCHED_NONE) */
     double absorption;         /* SPL_MODE_ABSORB: A_p = absorption * brightness * I_p, > 0 (default 1) */
+    int32_t log_flags;         /* SPL_LOG_I | SPL_LOG_S (default 0): logarithms of processed
+                                  quantities (Sec. 2) */
 } spl_params;
+
+/* log_flags: I is replaced by log10(I); s is replaced by log10(s) before its
+ * normalisation (s_min and s_max of the colour map are then in log units).  A
+ * non-positive value under a logarithm makes the particle inactive. */
+#define SPL_LOG_I 1
+#define SPL_LOG_S 2
 
 /* Per-frame statistics of the last render (counts are exact).  With timing
  * enabled (spl_set_timing) every render records CUDA events between its

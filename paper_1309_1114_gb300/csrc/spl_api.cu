@@ -60,11 +60,15 @@ struct spl_ctx {
     bool have_particles = false;
     DevBuf<float> x, y, z;
     DevBuf<unsigned char> h, I, s;
+    DevBuf<float> cr, cg, cb;          // optional colour components
+    bool have_rgb = false;
     // out-of-core rendering (spl_render_stream): two device chunks, filled on
     // a copy stream; while a chunk renders, the pipeline reads it instead of
     // the loaded SoA and adds into the image
     DevBuf<float> cx[2], cy[2], cz[2];
     DevBuf<unsigned char> ch[2], cI[2], cs[2];
+    DevBuf<float> ccr[2], ccg[2], ccb[2];
+    bool chunk_rgb = false;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copied[2] = {}, consumed[2] = {};
     bool streaming = false;
@@ -170,6 +174,7 @@ extern "C" int spl_default_params(spl_params *q) {
     q->mode = SPL_MODE_ADDITIVE;
     q->sched = SPL_SCHED_NONE;
     q->absorption = 1.0;
+    q->log_flags = 0;
     return SPL_OK;
 }
 
@@ -181,7 +186,7 @@ static bool params_ok(const spl_params *q) {
            q->r_small >= q->r_sml && std::isfinite(q->r_large) && q->r_large >= q->r_small &&
            (q->mode == SPL_MODE_ADDITIVE || q->mode == SPL_MODE_EA || q->mode == SPL_MODE_ABSORB) &&
            q->sched >= 0 && q->sched <= SPL_SCHED_MLP && std::isfinite(q->absorption) &&
-           q->absorption > 0;
+           q->absorption > 0 && q->log_flags >= 0 && q->log_flags <= (SPL_LOG_I | SPL_LOG_S);
 }
 
 static bool camera_ok(const spl_camera *c) {
@@ -251,9 +256,11 @@ extern "C" int spl_destroy(spl_ctx *c) {
     else cudaDeviceSynchronize();
     c->x.release(); c->y.release(); c->z.release();
     c->h.release(); c->I.release(); c->s.release();
+    c->cr.release(); c->cg.release(); c->cb.release();
     for (int b = 0; b < 2; ++b) {
         c->cx[b].release(); c->cy[b].release(); c->cz[b].release();
         c->ch[b].release(); c->cI[b].release(); c->cs[b].release();
+        c->ccr[b].release(); c->ccg[b].release(); c->ccb[b].release();
         if (c->copied[b]) cudaEventDestroy(c->copied[b]);
         if (c->consumed[b]) cudaEventDestroy(c->consumed[b]);
     }
@@ -287,6 +294,8 @@ extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
     if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
     if (p->mem_space != SPL_MEM_HOST && p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
+    const int nrgb = (p->cr != nullptr) + (p->cg != nullptr) + (p->cb != nullptr);
+    if (nrgb != 0 && nrgb != 3) return SPL_EINVAL;
     if (p->n > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // ids are 32-bit
     DeviceGuard g(c->device);
     const size_t n = (size_t)p->n;
@@ -308,7 +317,18 @@ extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
         SPL_CUDA(cudaMemcpyAsync(c->I.p, p->I, n * ab, kind, c->stream));
         SPL_CUDA(cudaMemcpyAsync(c->s.p, p->s, n * ab, kind, c->stream));
     }
+    if (nrgb == 3) {
+        SPL_TRY(c->cr.ensure(n ? n : 1));
+        SPL_TRY(c->cg.ensure(n ? n : 1));
+        SPL_TRY(c->cb.ensure(n ? n : 1));
+        if (n) {
+            SPL_CUDA(cudaMemcpyAsync(c->cr.p, p->cr, n * 4, kind, c->stream));
+            SPL_CUDA(cudaMemcpyAsync(c->cg.p, p->cg, n * 4, kind, c->stream));
+            SPL_CUDA(cudaMemcpyAsync(c->cb.p, p->cb, n * 4, kind, c->stream));
+        }
+    }
     SPL_CUDA(cudaStreamSynchronize(c->stream));
+    c->have_rgb = nrgb == 3;
     c->n = p->n;
     c->attr_type = p->attr_type;
     c->have_particles = true;
@@ -448,6 +468,7 @@ static FrameConst make_frame(const spl_ctx *c, const spl_camera &cam) {
     fc.r_large2 = (float)(q.r_large * q.r_large);
     fc.absorb = q.mode == SPL_MODE_ABSORB ? 1 : 0;
     fc.absorption = (float)q.absorption;
+    fc.log_flags = q.log_flags;
     if (fc.absorb) {
         // one list per tile: no small class, no separate large pass
         fc.r_small2 = fc.r_sml2;
@@ -559,9 +580,15 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
         const int b = c->chunk_buf;
         ra.x = c->cx[b].p; ra.y = c->cy[b].p; ra.z = c->cz[b].p;
         ra.h = c->ch[b].p; ra.I = c->cI[b].p; ra.s = c->cs[b].p;
+        if (c->chunk_rgb) {
+            ra.cr = c->ccr[b].p; ra.cg = c->ccg[b].p; ra.cb = c->ccb[b].p;
+        }
     } else {
         ra.x = c->x.p; ra.y = c->y.p; ra.z = c->z.p;
         ra.h = c->h.p; ra.I = c->I.p; ra.s = c->s.p;
+        if (c->have_rgb) {
+            ra.cr = c->cr.p; ra.cg = c->cg.p; ra.cb = c->cb.p;
+        }
     }
     ra.pal = c->pal.p;
     ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
@@ -764,6 +791,11 @@ static int copy_chunk(spl_ctx *c, const spl_particles *p, int64_t first, int64_t
                              cudaMemcpyHostToDevice, cs));
     SPL_CUDA(cudaMemcpyAsync(c->cs[b].p, (const unsigned char *)p->s + first * ab, m * ab,
                              cudaMemcpyHostToDevice, cs));
+    if (p->cr) {
+        SPL_CUDA(cudaMemcpyAsync(c->ccr[b].p, p->cr + first, m * 4, cudaMemcpyHostToDevice, cs));
+        SPL_CUDA(cudaMemcpyAsync(c->ccg[b].p, p->cg + first, m * 4, cudaMemcpyHostToDevice, cs));
+        SPL_CUDA(cudaMemcpyAsync(c->ccb[b].p, p->cb + first, m * 4, cudaMemcpyHostToDevice, cs));
+    }
     SPL_CUDA(cudaEventRecord(c->copied[b], cs));
     return SPL_OK;
 }
@@ -774,6 +806,8 @@ extern "C" int spl_render_stream(spl_ctx *c, const spl_particles *p, int64_t chu
     if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
     if (p->mem_space != SPL_MEM_HOST) return SPL_EINVAL;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
+    const int nrgb = (p->cr != nullptr) + (p->cg != nullptr) + (p->cb != nullptr);
+    if (nrgb != 0 && nrgb != 3) return SPL_EINVAL;
     if (!c->have_cam) return SPL_ESTATE;
     if (c->npal < 1) return SPL_ESTATE;
     if (c->par.mode == SPL_MODE_ABSORB) return SPL_EINVAL;   // not additive over chunks
@@ -796,6 +830,11 @@ extern "C" int spl_render_stream(spl_ctx *c, const spl_particles *p, int64_t chu
         SPL_TRY(c->ch[b].ensure((size_t)per * ah));
         SPL_TRY(c->cI[b].ensure((size_t)per * ab));
         SPL_TRY(c->cs[b].ensure((size_t)per * ab));
+        if (nrgb == 3) {
+            SPL_TRY(c->ccr[b].ensure((size_t)per));
+            SPL_TRY(c->ccg[b].ensure((size_t)per));
+            SPL_TRY(c->ccb[b].ensure((size_t)per));
+        }
         SPL_CUDA(cudaEventRecord(c->consumed[b], s));   // the buffers are free from here on
     }
     const int64_t nchunks = p->n > 0 ? (p->n + chunk - 1) / chunk : 1;
@@ -804,6 +843,7 @@ extern "C" int spl_render_stream(spl_ctx *c, const spl_particles *p, int64_t chu
     if (p->n > 0) rc = copy_chunk(c, p, 0, per < p->n ? per : p->n, 0);
     c->streaming = true;
     c->chunk_attr = p->attr_type;
+    c->chunk_rgb = nrgb == 3;
     for (int64_t k = 0; k < nchunks && rc == SPL_OK; ++k) {
         const int b = (int)(k & 1);
         const int64_t first = k * chunk;
@@ -861,6 +901,7 @@ static unsigned long long batch_key(const spl_ctx *c, const spl_camera *cams, in
     mix(&c->par, sizeof(c->par));
     mix(&c->n, sizeof(c->n));
     mix(&c->attr_type, sizeof(c->attr_type));
+    mix(&c->have_rgb, sizeof(c->have_rgb));
     mix(&c->npal, sizeof(c->npal));
     mix(&c->buf_gen, sizeof(c->buf_gen));
     return h;
@@ -1250,6 +1291,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     if (p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
     if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
+    if (((p->cr != nullptr) + (p->cg != nullptr) + (p->cb != nullptr)) % 3) return SPL_EINVAL;
     if (!camera_ok(cam)) return SPL_EINVAL;
     if (npal < 1 || npal > kMaxPalette || !std::isfinite(s_min) || !std::isfinite(s_max))
         return SPL_EINVAL;
@@ -1318,6 +1360,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     ra.n = p->n;
     ra.x = p->x; ra.y = p->y; ra.z = p->z;
     ra.h = p->h; ra.I = p->I; ra.s = p->s;
+    ra.cr = p->cr; ra.cg = p->cg; ra.cb = p->cb;
     ra.pal = pal;
     ra.rec0 = rec0; ra.rec1 = rec1;
     ra.counts = counts;

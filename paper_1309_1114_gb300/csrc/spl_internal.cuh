@@ -52,7 +52,7 @@ struct FrameConst {
     int slot_base;             // first list slot: slot = slot_base + list * ntiles + tile
     int absorb;                // general absorption (Eq. 1, E != A): one depth-sorted list per tile
     float absorption;          // A = absorption * brightness * I
-    int pad_;
+    int log_flags;             // 1: log10 of I, 2: log10 of s before normalisation
     long long rec_base;        // first record: record = rec_base + particle id
 };
 
@@ -115,6 +115,7 @@ struct RasterArgs {
     const float *x, *y, *z;
     const void *h, *I, *s;
     const float *pal;          // npal * 3
+    const float *cr, *cg, *cb; // optional per-particle colour components (replace the palette)
     float4 *rec0, *rec1;       // nviews * n records
     float2 *rec2;              // absorption mode: (A, depth key) per record, else null
     int *counts;               // list slots of all views: entries counted through the CTA tables

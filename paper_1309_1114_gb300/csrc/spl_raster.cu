@@ -78,8 +78,8 @@ __device__ __forceinline__ float load_attr(const void *p, int64_t i) {
 // absorption * brightness * I, the key z_c rounded to float (the double-float
 // value's leading part).
 __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spal, float x, float y,
-                                          float z, float h, float inten, float s, float4 &r0,
-                                          float4 &r1, float2 &q2) {
+                                          float z, float h, float inten, float s, const float *crgb,
+                                          float4 &r0, float4 &r1, float2 &q2) {
     // roto-translation x_c = R x - R eye, in df
     df c[3];
 #pragma unroll
@@ -96,8 +96,18 @@ __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spa
     if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(h) || !isfinite(inten) ||
         !isfinite(s) || h < 0.f)
         return CLS_INACTIVE;
+    if (crgb && (!isfinite(crgb[0]) || !isfinite(crgb[1]) || !isfinite(crgb[2]))) return CLS_INACTIVE;
     const float zc = c[2].hi;
     if (!(zc > fc.z_near)) return CLS_INACTIVE;
+    // logarithms of processed quantities (Sec. 2)
+    if (fc.log_flags & 1) {
+        if (!(inten > 0.f)) return CLS_INACTIVE;
+        inten = log10f(inten);
+    }
+    if (fc.log_flags & 2) {
+        if (!(s > 0.f)) return CLS_INACTIVE;
+        s = log10f(s);
+    }
     // perspective projection
     const df f = {fc.fhi, fc.flo};
     df xs = df_add({fc.half_w, 0.f}, df_mul(f, df_div(c[0], c[2])));
@@ -112,7 +122,9 @@ __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spa
     // colour: normalise, palette look-up, scale by intensity (Sec. 2)
     float sn = fminf(fmaxf((s - fc.s_min) * fc.s_inv, 0.f), 1.f);
     float col[3];
-    if (fc.npal == 1) {
+    if (crgb) {
+        col[0] = crgb[0]; col[1] = crgb[1]; col[2] = crgb[2];
+    } else if (fc.npal == 1) {
         col[0] = spal[0]; col[1] = spal[1]; col[2] = spal[2];
     } else {
         float u = sn * (float)(fc.npal - 1);
@@ -253,8 +265,8 @@ __device__ __forceinline__ void load_view(const FrameConst *fcs, int v, FrameCon
 // every view of the batch (its inputs are read from HBM once and then hit in
 // L2), records are written to rec[view * n + id], list entries are counted.
 // ATTR: 0 = h, I, s in FP32; 1 = all three in binary16; 2 = h in FP32, I and s
-// in binary16.
-template <int ATTR>
+// in binary16.  RGB: per-particle colour components replace the palette.
+template <int ATTR, bool RGB>
 __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) {
     __shared__ float spal[3 * kMaxPalette];
     __shared__ int keys[kHash], vals[kHash];
@@ -280,9 +292,13 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
             const int64_t rec = fc.rec_base + i;
             if (valid) {
                 float2 q2;
+                float crgb[3] = {0.f, 0.f, 0.f};
+                if (RGB) {
+                    crgb[0] = a.cr[i]; crgb[1] = a.cg[i]; crgb[2] = a.cb[i];
+                }
                 cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_attr<ATTR == 1>(a.h, i),
-                                 load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i), r0, r1,
-                                 q2);
+                                 load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i),
+                                 RGB ? crgb : nullptr, r0, r1, q2);
                 a.rec0[rec] = r0;
                 a.rec1[rec] = r1;
                 if (a.rec2) a.rec2[rec] = q2;
@@ -334,12 +350,17 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
 void launch_raster(const Views &vs, const RasterArgs &a, int attr, cudaStream_t s) {
     if (a.n <= 0 || vs.nviews <= 0) return;
     const int64_t blocks = (a.n + kChunk - 1) / kChunk;
-    if (attr == 1)
-        raster_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
-    else if (attr == 2)
-        raster_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
-    else
-        raster_kernel<0><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+    const bool rgb = a.cr != nullptr;
+    if (attr == 1) {
+        if (rgb) raster_kernel<1, true><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+        else raster_kernel<1, false><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+    } else if (attr == 2) {
+        if (rgb) raster_kernel<2, true><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+        else raster_kernel<2, false><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+    } else {
+        if (rgb) raster_kernel<0, true><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+        else raster_kernel<0, false><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+    }
 }
 
 // ---------------------------------------------------------------------------

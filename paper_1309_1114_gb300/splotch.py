@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_PKG, "lib", "libsplotch.so")
 SPL_OK, SPL_EINVAL, SPL_ENOMEM, SPL_ECUDA, SPL_ESTATE, SPL_EDEVICE, SPL_ELIMIT = range(7)
 SPL_MEM_HOST, SPL_MEM_DEVICE = 0, 1
 SPL_ATTR_F32, SPL_ATTR_F16, SPL_ATTR_F16_IS = 0, 1, 2
-SPL_MODE_ADDITIVE, SPL_MODE_EA = 0, 1
+SPL_MODE_ADDITIVE, SPL_MODE_EA, SPL_MODE_ABSORB = 0, 1, 2
+SPL_LOG_I, SPL_LOG_S = 1, 2
 SPL_SCHED_NONE, SPL_SCHED_COUNT, SPL_SCHED_MLP = 0, 1, 2
 SPL_MLP_NPARAM = 2177
 
@@ -27,7 +28,8 @@ SPL_MLP_NPARAM = 2177
 class spl_particles(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("h", C.c_void_p), ("I", C.c_void_p), ("s", C.c_void_p),
-                ("attr_type", C.c_int32), ("mem_space", C.c_int32)]
+                ("attr_type", C.c_int32), ("mem_space", C.c_int32),
+                ("cr", C.c_void_p), ("cg", C.c_void_p), ("cb", C.c_void_p)]
 
 
 class spl_camera(C.Structure):
@@ -40,7 +42,7 @@ class spl_params(C.Structure):
     _fields_ = [("chi", C.c_double), ("sigma_per_h", C.c_double), ("s_box", C.c_double),
                 ("r_sml", C.c_double), ("brightness", C.c_double), ("tile_px", C.c_int32),
                 ("r_small", C.c_double), ("r_large", C.c_double), ("mode", C.c_int32),
-                ("sched", C.c_int32), ("absorption", C.c_double)]
+                ("sched", C.c_int32), ("absorption", C.c_double), ("log_flags", C.c_int32)]
 
 
 class spl_stats(C.Structure):
@@ -220,6 +222,17 @@ class Renderer:
                     raise ValueError("particle arrays: wrong dtype or shape")
         p = spl_particles(n, *[_ptr(a) for a in arrs], attr,
                           SPL_MEM_DEVICE if any(on_dev) else SPL_MEM_HOST)
+        if "cr" in src:
+            # per-particle colour components (FP32, same memory space as the rest)
+            rgb = [src[k] for k in ("cr", "cg", "cb")]
+            if any(hasattr(a, "is_cuda") and a.is_cuda for a in rgb) != any(on_dev):
+                raise ValueError("colour components must live where the particles do")
+            if not any(on_dev):
+                rgb = [np.ascontiguousarray(a, dtype=np.float32) for a in rgb]
+            if any(tuple(a.shape) != (n,) for a in rgb):
+                raise ValueError("colour components: wrong shape")
+            p.cr, p.cg, p.cb = (_ptr(a) for a in rgb)
+            arrs = arrs + rgb
         return p, arrs
 
     def load(self, parts: dict, fp16: dict | None = None):
