@@ -41,6 +41,9 @@ WORKLOADS = {
                   "desc": "100M clustered particles, h/I/s stored FP16, 2048x2048 RGB FP32"},
     "precision-mixed": {"scene": "precision", "label": "clustered-100M-2048sq-f16IS", "fp16": "is",
                         "desc": "100M clustered particles, I/s stored FP16, h FP32, 2048x2048 RGB FP32"},
+    "precision-logh": {"scene": "precision", "label": "clustered-100M-2048sq-logh16", "fp16": "logh",
+                       "desc": "100M clustered particles, I/s stored FP16, h as a 16-bit logarithmic "
+                               "code (1/4096 octave), 2048x2048 RGB FP32"},
     "precision32": {"scene": "precision", "label": "clustered-100M-2048sq-f32",
                     "desc": "100M clustered particles, FP32 attributes, 2048x2048 RGB FP32"},
     "absorb": {"scene": "clustered", "label": "clustered-10M-1024sq-f32-absorb",
@@ -408,13 +411,19 @@ def run_ours(args, wl):
     cam = scene.cams[0]
     W, H = cam["width"], cam["height"]
     fp16 = None
+    h_log2_min = None
     if wl.get("fp16") == "all":
         fp16 = scene.fp16
     elif wl.get("fp16") == "is":
         fp16 = {k: scene.fp16[k] for k in ("I", "s")}
+    elif wl.get("fp16") == "logh":
+        from paper_1309_1114_gb300 import scenes as _sc
+        h_log2_min = -14.0
+        fp16 = {"h": _sc.log16_h(scene.parts["h"], h_log2_min), "I": scene.fp16["I"],
+                "s": scene.fp16["s"]}
     stream = torch.cuda.current_stream()
     r = Renderer(local, stream.cuda_stream)
-    r.load(scene.parts, fp16)
+    r.load(scene.parts, fp16, h_log2_min)
     r.set_colormap(scene.palette)
     r.set_camera(cam)
     r.set_params(**wl.get("params", {}))
@@ -502,7 +511,7 @@ def run_ours(args, wl):
             r.set_timing(False)
             schedulers[name] = sst["sum_ms"][5] / max(sst["timed_frames"], 1)
         r.set_params(sched=sched_mode)
-    bytes_per_particle = {None: 24, "all": 18, "is": 20}[wl.get("fp16")]
+    bytes_per_particle = {None: 24, "all": 18, "is": 20, "logh": 18}[wl.get("fp16")]
     alg_bytes = scene.n * bytes_per_particle + 12 * W * H
     hbm = float(peaks.get("hbm_gbs", 6771.1))
     hbm_frac = alg_bytes / (ms * 1e-3) / (hbm * 1e9)
@@ -525,7 +534,7 @@ def run_ours(args, wl):
             r.load(dict(xyz, **attrs))
         else:
             r.load(dict(xyz, **{k: attrs[k] for k in attrs if k not in fp16}),
-                   {k: attrs[k] for k in fp16})
+                   {k: attrs[k] for k in fp16}, h_log2_min)
         r.render_host(host_np)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if ws > 1:
@@ -551,7 +560,8 @@ def run_ours(args, wl):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["label"], "description": wl["desc"],
                        "n_particles": scene.n, "image": [W, H],
-                       "attributes": {None: "f32", "all": "h,I,s f16", "is": "I,s f16; h f32"}[wl.get("fp16")],
+                       "attributes": {None: "f32", "all": "h,I,s f16", "is": "I,s f16; h f32",
+                                      "logh": "I,s f16; h 16-bit log code"}[wl.get("fp16")],
                        "tile_px": 32, "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (particles + per-frame records > 129 MB); no flush"},
             "roofline": roofline,

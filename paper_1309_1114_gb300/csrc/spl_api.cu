@@ -57,6 +57,7 @@ struct spl_ctx {
     // particles (SoA)
     int64_t n = 0;
     int attr_type = SPL_ATTR_F32;
+    float h_log2_min = 0.f;            // SPL_ATTR_LOGH16
     bool have_particles = false;
     DevBuf<float> x, y, z;
     DevBuf<unsigned char> h, I, s;
@@ -75,6 +76,7 @@ struct spl_ctx {
     int chunk_buf = 0;
     int64_t chunk_n = 0;
     int chunk_attr = SPL_ATTR_F32;
+    float chunk_h_log2_min = 0.f;
     bool accumulate = false;      // the image already holds earlier chunks
     bool last_chunk = true;       // apply the E=A map after this render
     // colour map
@@ -291,7 +293,8 @@ extern "C" int spl_destroy(spl_ctx *c) {
 
 extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
     if (!c || !p || p->n < 0) return SPL_EINVAL;
-    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
+    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_LOGH16) return SPL_EINVAL;
+    if (p->attr_type == SPL_ATTR_LOGH16 && !std::isfinite(p->h_log2_min)) return SPL_EINVAL;
     if (p->mem_space != SPL_MEM_HOST && p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
     const int nrgb = (p->cr != nullptr) + (p->cg != nullptr) + (p->cb != nullptr);
@@ -299,7 +302,7 @@ extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
     if (p->n > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // ids are 32-bit
     DeviceGuard g(c->device);
     const size_t n = (size_t)p->n;
-    const size_t ah = p->attr_type == SPL_ATTR_F16 ? 2 : 4;     // bytes of h
+    const size_t ah = (p->attr_type == SPL_ATTR_F16 || p->attr_type == SPL_ATTR_LOGH16) ? 2 : 4;
     const size_t ab = p->attr_type == SPL_ATTR_F32 ? 4 : 2;     // bytes of I and s
     SPL_TRY(c->x.ensure(n ? n : 1));
     SPL_TRY(c->y.ensure(n ? n : 1));
@@ -331,6 +334,7 @@ extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
     c->have_rgb = nrgb == 3;
     c->n = p->n;
     c->attr_type = p->attr_type;
+    c->h_log2_min = p->h_log2_min;
     c->have_particles = true;
     return SPL_OK;
 }
@@ -583,12 +587,14 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
         if (c->chunk_rgb) {
             ra.cr = c->ccr[b].p; ra.cg = c->ccg[b].p; ra.cb = c->ccb[b].p;
         }
+        ra.h_log2_min = c->chunk_h_log2_min;
     } else {
         ra.x = c->x.p; ra.y = c->y.p; ra.z = c->z.p;
         ra.h = c->h.p; ra.I = c->I.p; ra.s = c->s.p;
         if (c->have_rgb) {
             ra.cr = c->cr.p; ra.cg = c->cg.p; ra.cb = c->cb.p;
         }
+        ra.h_log2_min = c->h_log2_min;
     }
     ra.pal = c->pal.p;
     ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
@@ -777,7 +783,7 @@ extern "C" int spl_render_host(spl_ctx *c, float *h_image) {
 // adds its additive image into d_image (the sum is linear in the particle
 // set, Sec. 2); the E=A map, if selected, follows the last chunk.
 static int copy_chunk(spl_ctx *c, const spl_particles *p, int64_t first, int64_t cnt, int b) {
-    const size_t ah = p->attr_type == SPL_ATTR_F16 ? 2 : 4;
+    const size_t ah = (p->attr_type == SPL_ATTR_F16 || p->attr_type == SPL_ATTR_LOGH16) ? 2 : 4;
     const size_t ab = p->attr_type == SPL_ATTR_F32 ? 4 : 2;
     const size_t m = (size_t)cnt;
     cudaStream_t cs = c->copy_stream;
@@ -803,7 +809,8 @@ static int copy_chunk(spl_ctx *c, const spl_particles *p, int64_t first, int64_t
 extern "C" int spl_render_stream(spl_ctx *c, const spl_particles *p, int64_t chunk, float *d_image,
                                  void *stream) {
     if (!c || !p || !d_image || chunk < 1 || p->n < 0) return SPL_EINVAL;
-    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
+    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_LOGH16) return SPL_EINVAL;
+    if (p->attr_type == SPL_ATTR_LOGH16 && !std::isfinite(p->h_log2_min)) return SPL_EINVAL;
     if (p->mem_space != SPL_MEM_HOST) return SPL_EINVAL;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
     const int nrgb = (p->cr != nullptr) + (p->cg != nullptr) + (p->cb != nullptr);
@@ -821,7 +828,7 @@ extern "C" int spl_render_stream(spl_ctx *c, const spl_particles *p, int64_t chu
         }
     }
     const int64_t per = p->n < chunk ? (p->n > 0 ? p->n : 1) : chunk;
-    const size_t ah = p->attr_type == SPL_ATTR_F16 ? 2 : 4;
+    const size_t ah = (p->attr_type == SPL_ATTR_F16 || p->attr_type == SPL_ATTR_LOGH16) ? 2 : 4;
     const size_t ab = p->attr_type == SPL_ATTR_F32 ? 4 : 2;
     for (int b = 0; b < 2; ++b) {
         SPL_TRY(c->cx[b].ensure((size_t)per));
@@ -843,6 +850,7 @@ extern "C" int spl_render_stream(spl_ctx *c, const spl_particles *p, int64_t chu
     if (p->n > 0) rc = copy_chunk(c, p, 0, per < p->n ? per : p->n, 0);
     c->streaming = true;
     c->chunk_attr = p->attr_type;
+    c->chunk_h_log2_min = p->h_log2_min;
     c->chunk_rgb = nrgb == 3;
     for (int64_t k = 0; k < nchunks && rc == SPL_OK; ++k) {
         const int b = (int)(k & 1);
@@ -902,6 +910,7 @@ static unsigned long long batch_key(const spl_ctx *c, const spl_camera *cams, in
     mix(&c->n, sizeof(c->n));
     mix(&c->attr_type, sizeof(c->attr_type));
     mix(&c->have_rgb, sizeof(c->have_rgb));
+    mix(&c->h_log2_min, sizeof(c->h_log2_min));
     mix(&c->npal, sizeof(c->npal));
     mix(&c->buf_gen, sizeof(c->buf_gen));
     return h;
@@ -1289,7 +1298,8 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
                                   float s_max, float *d_image, int32_t device, void *stream) {
     if (!p || !cam || !rgb || !d_image || p->n < 0) return SPL_EINVAL;
     if (p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
-    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_F16_IS) return SPL_EINVAL;
+    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_LOGH16) return SPL_EINVAL;
+    if (p->attr_type == SPL_ATTR_LOGH16 && !std::isfinite(p->h_log2_min)) return SPL_EINVAL;
     if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
     if (((p->cr != nullptr) + (p->cg != nullptr) + (p->cb != nullptr)) % 3) return SPL_EINVAL;
     if (!camera_ok(cam)) return SPL_EINVAL;
@@ -1361,6 +1371,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     ra.x = p->x; ra.y = p->y; ra.z = p->z;
     ra.h = p->h; ra.I = p->I; ra.s = p->s;
     ra.cr = p->cr; ra.cg = p->cg; ra.cb = p->cb;
+    ra.h_log2_min = p->h_log2_min;
     ra.pal = pal;
     ra.rec0 = rec0; ra.rec1 = rec1;
     ra.counts = counts;

@@ -116,6 +116,7 @@ struct RasterArgs {
     const void *h, *I, *s;
     const float *pal;          // npal * 3
     const float *cr, *cg, *cb; // optional per-particle colour components (replace the palette)
+    float h_log2_min;          // ATTR 3: h = 2^(h_log2_min + code / 4096)
     float4 *rec0, *rec1;       // nviews * n records
     float2 *rec2;              // absorption mode: (A, depth key) per record, else null
     int *counts;               // list slots of all views: entries counted through the CTA tables

@@ -73,6 +73,15 @@ __device__ __forceinline__ float load_attr(const void *p, int64_t i) {
     return static_cast<const float *>(p)[i];
 }
 
+// Smoothing length of particle i: FP32 (ATTR 0, 2), binary16 (ATTR 1), or a
+// 16-bit logarithmic code k with h = 2^(h_log2_min + k / 4096) (ATTR 3).
+template <int ATTR>
+__device__ __forceinline__ float load_h(const void *p, int64_t i, float h_log2_min) {
+    if (ATTR == 3)
+        return exp2f(fmaf((float)static_cast<const unsigned short *>(p)[i], 1.f / 4096.f, h_log2_min));
+    return load_attr<ATTR == 1>(p, i);
+}
+
 // Rasterise one particle into its record; returns its class.  q2 receives
 // (absorption coefficient A, depth key) for the absorption mode: A =
 // absorption * brightness * I, the key z_c rounded to float (the double-float
@@ -265,7 +274,8 @@ __device__ __forceinline__ void load_view(const FrameConst *fcs, int v, FrameCon
 // every view of the batch (its inputs are read from HBM once and then hit in
 // L2), records are written to rec[view * n + id], list entries are counted.
 // ATTR: 0 = h, I, s in FP32; 1 = all three in binary16; 2 = h in FP32, I and s
-// in binary16.  RGB: per-particle colour components replace the palette.
+// in binary16; 3 = h as a 16-bit logarithmic code, I and s in binary16.  RGB:
+// per-particle colour components replace the palette.
 template <int ATTR, bool RGB>
 __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) {
     __shared__ float spal[3 * kMaxPalette];
@@ -296,7 +306,7 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
                 if (RGB) {
                     crgb[0] = a.cr[i]; crgb[1] = a.cg[i]; crgb[2] = a.cb[i];
                 }
-                cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_attr<ATTR == 1>(a.h, i),
+                cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_h<ATTR>(a.h, i, a.h_log2_min),
                                  load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i),
                                  RGB ? crgb : nullptr, r0, r1, q2);
                 a.rec0[rec] = r0;
@@ -357,6 +367,9 @@ void launch_raster(const Views &vs, const RasterArgs &a, int attr, cudaStream_t 
     } else if (attr == 2) {
         if (rgb) raster_kernel<2, true><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
         else raster_kernel<2, false><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+    } else if (attr == 3) {
+        if (rgb) raster_kernel<3, true><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
+        else raster_kernel<3, false><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
     } else {
         if (rgb) raster_kernel<0, true><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
         else raster_kernel<0, false><<<(unsigned)blocks, 256, 0, s>>>(vs, a);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "lib", "libsplotch.so")
 
 SPL_OK, SPL_EINVAL, SPL_ENOMEM, SPL_ECUDA, SPL_ESTATE, SPL_EDEVICE, SPL_ELIMIT = range(7)
 SPL_MEM_HOST, SPL_MEM_DEVICE = 0, 1
-SPL_ATTR_F32, SPL_ATTR_F16, SPL_ATTR_F16_IS = 0, 1, 2
+SPL_ATTR_F32, SPL_ATTR_F16, SPL_ATTR_F16_IS, SPL_ATTR_LOGH16 = 0, 1, 2, 3
 SPL_MODE_ADDITIVE, SPL_MODE_EA, SPL_MODE_ABSORB = 0, 1, 2
 SPL_LOG_I, SPL_LOG_S = 1, 2
 SPL_SCHED_NONE, SPL_SCHED_COUNT, SPL_SCHED_MLP = 0, 1, 2
@@ -29,7 +29,8 @@ class spl_particles(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("h", C.c_void_p), ("I", C.c_void_p), ("s", C.c_void_p),
                 ("attr_type", C.c_int32), ("mem_space", C.c_int32),
-                ("cr", C.c_void_p), ("cg", C.c_void_p), ("cb", C.c_void_p)]
+                ("cr", C.c_void_p), ("cg", C.c_void_p), ("cb", C.c_void_p),
+                ("h_log2_min", C.c_float)]
 
 
 class spl_camera(C.Structure):
@@ -198,15 +199,20 @@ class Renderer:
         return self._h
 
     @staticmethod
-    def _particles(parts: dict, fp16: dict | None):
+    def _particles(parts: dict, fp16: dict | None, h_log2_min: float | None = None):
         """spl_particles for parts (and the arrays it points to, kept alive by
         the caller).  fp16 (optional) holds binary16 arrays that replace parts'
-        h, I and s (SPL_ATTR_F16), or only I and s (SPL_ATTR_F16_IS)."""
+        h, I and s (SPL_ATTR_F16), or only I and s (SPL_ATTR_F16_IS); with
+        h_log2_min, fp16["h"] holds 16-bit logarithmic codes (SPL_ATTR_LOGH16)."""
         src = dict(parts)
         attr = SPL_ATTR_F32
         if fp16 is not None:
             src.update(fp16)
             attr = SPL_ATTR_F16 if "h" in fp16 else SPL_ATTR_F16_IS
+            if h_log2_min is not None:
+                if "h" not in fp16:
+                    raise ValueError("logarithmic h codes go in fp16['h']")
+                attr = SPL_ATTR_LOGH16
         arrs = [src[k] for k in ("x", "y", "z", "h", "I", "s")]
         on_dev = [hasattr(a, "is_cuda") and a.is_cuda for a in arrs]
         if any(on_dev) and not all(on_dev):
@@ -214,14 +220,16 @@ class Renderer:
         n = int(arrs[0].shape[0])
         if not any(on_dev):
             arrs = [np.ascontiguousarray(a) for a in arrs]
-            half_h = attr == SPL_ATTR_F16
-            wants = [np.float32] * 3 + [np.float16 if half_h else np.float32] + \
+            want_h = {SPL_ATTR_F16: np.float16, SPL_ATTR_LOGH16: np.uint16}.get(attr, np.float32)
+            wants = [np.float32] * 3 + [want_h] + \
                 [np.float16 if attr != SPL_ATTR_F32 else np.float32] * 2
             for a, want in zip(arrs, wants):
                 if a.dtype != want or a.shape != (n,):
                     raise ValueError("particle arrays: wrong dtype or shape")
         p = spl_particles(n, *[_ptr(a) for a in arrs], attr,
                           SPL_MEM_DEVICE if any(on_dev) else SPL_MEM_HOST)
+        if h_log2_min is not None:
+            p.h_log2_min = float(h_log2_min)
         if "cr" in src:
             # per-particle colour components (FP32, same memory space as the rest)
             rgb = [src[k] for k in ("cr", "cg", "cb")]
@@ -235,9 +243,9 @@ class Renderer:
             arrs = arrs + rgb
         return p, arrs
 
-    def load(self, parts: dict, fp16: dict | None = None):
+    def load(self, parts: dict, fp16: dict | None = None, h_log2_min: float | None = None):
         """Load particles (host or device arrays; see _particles for fp16)."""
-        p, keep = self._particles(parts, fp16)
+        p, keep = self._particles(parts, fp16, h_log2_min)
         check(load_library().spl_load_particles(self._h, C.byref(p)), "spl_load_particles")
         del keep
 

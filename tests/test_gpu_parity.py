@@ -35,8 +35,8 @@ def rnd(torch_cuda):
     r.close()
 
 
-def gpu_render(r, torch, parts, pal, cam, fp16=None, **params):
-    r.load(parts, fp16)
+def gpu_render(r, torch, parts, pal, cam, fp16=None, h_log2_min=None, **params):
+    r.load(parts, fp16, h_log2_min)
     r.set_colormap(pal)
     r.set_params(**params)
     r.set_camera(cam)
@@ -213,9 +213,9 @@ def test_clustered_reduced_full_image(rnd, torch_cuda):
 
 
 def sampled_check(r, torch, sc, cam, n_sample=96, tol=TOL32, fp16=None, parts_oracle=None,
-                  **params):
+                  h_log2_min=None, **params):
     """Full-size render, compared at sampled pixels computed one by one."""
-    g = gpu_render(r, torch, sc.parts, sc.palette, cam, fp16=fp16, **params)
+    g = gpu_render(r, torch, sc.parts, sc.palette, cam, fp16=fp16, h_log2_min=h_log2_min, **params)
     rng = np.random.default_rng(0)
     H, W = cam["height"], cam["width"]
     flat = g[..., 0].ravel()
