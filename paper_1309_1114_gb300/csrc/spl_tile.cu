@@ -567,13 +567,16 @@ void launch_epilogue_ea(float *image, int64_t nvals, int sms, cudaStream_t s) {
 template <int T>
 __device__ __forceinline__ void absorb_tabulate(const FrameConst &fc, const float4 *st0,
                                                 const float4 *st1, const float2 *st2, int cnt,
-                                                int x0, int y0, float2 (*swx)[T], float2 (*srow)[T],
-                                                float4 *ssrc, unsigned *band_mask, int tid) {
+                                                int x0, int y0, float2 (*swx)[Shape<T>::WXS],
+                                                float2 (*srow)[Shape<T>::WXS], float4 *ssrc,
+                                                unsigned *band_mask, int tid) {
     using S = Shape<T>;
     const int p = tid >> 3, q = tid & 7;
-    if (p >= cnt) return;
-    const float4 r0 = st0[p], r1 = st1[p];
-    const float A = st2[p].x, r2 = r1.x;
+    // every lane runs to the end (band bits by ballot); entries of p >= cnt are
+    // written but never read
+    const bool valid = p < cnt;
+    const float4 r0 = st0[valid ? p : 0], r1 = st1[valid ? p : 0];
+    const float A = st2[valid ? p : 0].x, r2 = r1.x;
     const bool point = r2 <= fc.r_sml2;
     const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
     if (q == 0) {
@@ -581,6 +584,7 @@ __device__ __forceinline__ void absorb_tabulate(const FrameConst &fc, const floa
         ssrc[p] = make_float4(r1.y * inv, r1.z * inv, r1.w * inv, 0.f);
     }
     int ilo, ihi, jlo, jhi;
+    float r = 0.f, xh = 0.f, yh = 0.f;
     if (point) {
         ilo = ihi = xi - x0;
         jlo = jhi = yi - y0;
@@ -592,8 +596,9 @@ __device__ __forceinline__ void absorb_tabulate(const FrameConst &fc, const floa
         }
     } else {
         const float kq = r0.w, B = __fdividef(1048576.f, r2);
-        const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
-        const float r = r2 * rsqrtf(r2) + 1e-3f;   // approximate: far inside the margin
+        xh = 0.5f - r0.y;
+        yh = 0.5f - r0.z;
+        r = r2 * rsqrtf(r2) + 1e-3f;   // approximate: far inside the margin
         ilo = xi - x0 + (int)ceilf(fmaxf(r0.y - 0.5f - r, -1e6f));
         ihi = xi - x0 + (int)floorf(fminf(r0.y - 0.5f + r, 1e6f));
         jlo = yi - y0 + (int)ceilf(fmaxf(r0.z - 0.5f - r, -1e6f));
@@ -609,9 +614,24 @@ __device__ __forceinline__ void absorb_tabulate(const FrameConst &fc, const floa
             srow[p][k] = make_float2(A * ex2_neg(kq * dy2), fmaf(r2 - dy2, B, 1.f));
         }
     }
+    // band q: box overlap, and for a disc its reach to the band's nearest pixel
+    // centre (as in the additive pass); a warp's four particles by one ballot
     const int bx0 = (q % S::NBX) * S::BW, by0 = (q / S::NBX) * S::BH;
     const int bx1 = bx0 + S::BW - 1, by1 = by0 + S::BH - 1;
-    if (jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1) atomicOr(&band_mask[q], 1u << p);
+    bool hit = valid && jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1;
+    if (!point) {
+        const float ax = (float)(x0 + bx0 - xi) + xh, ay = (float)(y0 + by0 - yi) + yh;
+        const float nx = fmaxf(ax, fminf(0.f, ax + (float)(S::BW - 1)));
+        const float ny = fmaxf(ay, fminf(0.f, ay + (float)(S::BH - 1)));
+        hit = hit && nx * nx + ny * ny <= r * r;
+    }
+    const unsigned hb = __ballot_sync(0xffffffffu, hit);
+    const int lane = tid & 31;
+    if (lane < 8) {
+        const unsigned nib = ((hb >> lane) & 1u) | (((hb >> (lane + 8)) & 1u) << 1) |
+                             (((hb >> (lane + 16)) & 1u) << 2) | (((hb >> (lane + 24)) & 1u) << 3);
+        if (nib) atomicOr(&band_mask[lane], nib << (4 * (tid >> 5)));
+    }
 }
 
 // 1 - exp(-tau) for tau >= 0 with small relative error everywhere: below
@@ -627,7 +647,7 @@ __device__ __forceinline__ float one_minus_exp_neg(float tau) {
 template <int T>
 __host__ __device__ constexpr size_t absorb_smem_bytes() {
     using S = Shape<T>;
-    return (sizeof(float2) * 2 * T + sizeof(float4)) * S::P +   // swx, srow, ssrc
+    return (sizeof(float2) * 2 * S::WXS + sizeof(float4)) * S::P +   // swx, srow, ssrc
            (2 * sizeof(float4) + sizeof(float2)) * S::P;          // staged records
 }
 
@@ -635,8 +655,8 @@ template <int T>
 __global__ void __launch_bounds__(kTileThreads, 2) absorb_kernel(Views vs, TileArgs a) {
     using S = Shape<T>;
     extern __shared__ float4 smem_raw[];
-    float2 (*swx)[T] = reinterpret_cast<float2 (*)[T]>(smem_raw);
-    float2 (*srow)[T] = swx + S::P;
+    float2 (*swx)[S::WXS] = reinterpret_cast<float2 (*)[S::WXS]>(smem_raw);
+    float2 (*srow)[S::WXS] = swx + S::P;
     float4 *ssrc = reinterpret_cast<float4 *>(srow + S::P);
     float4 *st0 = ssrc + S::P;
     float4 *st1 = st0 + S::P;
