@@ -236,3 +236,25 @@ def test_clustered_full_size_sampled(rnd, torch_cuda):
     assert err <= TOL32, err
     st = rnd.stats()
     assert st["n_active"] > 0.9 * sc.n
+
+
+@pytest.mark.parametrize("w,h,tile", [(16384, 48, 32), (40, 16384, 64), (16384, 16384, 16)])
+def test_extreme_image_sides(rnd, torch_cuda, w, h, tile):
+    # the largest side the camera accepts and extreme aspect ratios: pixel and
+    # tile indices far from the origin, ragged last tiles; a few thousand
+    # particles keep the oracle quick
+    parts, cam = random_scene(31 + w % 7, 4000, w, h, hmin=-9.0, hmax=-4.0)
+    if w * h > 64_000_000:
+        # the full 16384^2 image: compare sampled pixels and check the rest is finite
+        g = gpu_render(rnd, torch_cuda, parts, scenes.ramp_palette(), cam, tile_px=tile)
+        assert np.isfinite(g).all()
+        ys, xs = np.nonzero(g[..., 0] > 0)
+        rng = np.random.default_rng(0)
+        pick = rng.choice(len(xs), min(256, len(xs)), replace=False)
+        px, py = xs[pick].astype(np.int32), ys[pick].astype(np.int32)
+        o = oracle.render_pixels(parts, scenes.ramp_palette(), cam, {}, px, py,
+                                 nthreads=os.cpu_count() or 1)
+        M = np.abs(g).reshape(-1, 3).max(0)
+        assert rel_pixel_error(g[py, px], o, M=M) <= TOL32
+        return
+    check_image(rnd, torch_cuda, parts, scenes.ramp_palette(), cam, tile_px=tile)
