@@ -286,6 +286,7 @@ def run_batch(args, wl):
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    graph_kernels = int(r.stats()["launches"])      # kernel nodes of the replayed graph
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -387,7 +388,7 @@ def run_batch(args, wl):
             "hbm_alg_bytes_per_step": alg_bytes,
             "stage_ms": stage,
             "e2e": e2e,
-            "gpu_launches": 11 * args.steps,
+            "gpu_launches": graph_kernels * args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

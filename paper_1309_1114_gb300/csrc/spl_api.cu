@@ -116,6 +116,7 @@ struct spl_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     unsigned long long graph_key = 0;   // configuration the graph was captured for
+    int graph_kernels = 0;              // kernel nodes of the captured graph
     unsigned long long buf_gen = 0;     // bumped whenever a scratch buffer moves
     bool use_graph = true;
     // scheduling of the work items, and the per-item samples that train it
@@ -136,6 +137,8 @@ struct spl_ctx {
     float last_ms[6] = {};
     spl_stats last{};
 };
+
+thread_local long long spl::g_launches = 0;
 
 static int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return SPL_OK;
@@ -711,6 +714,7 @@ static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const 
     Views vs{};
     SPL_TRY(prepare_views(c, cams, V, images, vs));
     SPL_CUDA(cudaGetLastError());
+    const long long launched0 = g_launches;
     record_event(c, 0, s);
     enqueue_binning(c, vs, s);
     SPL_CUDA(cudaGetLastError());
@@ -738,11 +742,7 @@ static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const 
     c->last_items = n_tile_items + n_large_items;
     enqueue_render(c, vs, n_large_items > 0, s);
     SPL_CUDA(cudaGetLastError());
-    const int launches = 4 + (c->accumulate ? 0 : 1) + (src_n(c) > 0 ? 4 : 0) + 1 +
-                         (n_large_items > 0 ? 1 : 0) +
-                         (c->par.mode == SPL_MODE_EA && c->last_chunk ? 1 : 0) +
-                         (c->par.sched != SPL_SCHED_NONE || c->recording ? 1 : 0) +
-                         (c->par.sched != SPL_SCHED_NONE ? 4 : 0);
+    const int launches = (int)(g_launches - launched0);
     if (c->timing) {
         c->ev_pending[c->ev_set] = true;
         c->ev_set ^= 1;
@@ -928,8 +928,10 @@ static int capture_batch(spl_ctx *c, const Views &vs, unsigned long long key) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
+        const long long launched0 = g_launches;
         enqueue_binning(c, vs, c->cap_stream);
         enqueue_render(c, vs, true, c->cap_stream);
+        c->graph_kernels = (int)(g_launches - launched0);
         e = cudaStreamEndCapture(c->cap_stream, &g);
     }
     c->timing = timing;
@@ -976,7 +978,7 @@ extern "C" int spl_render_batch(spl_ctx *c, const spl_camera *cams, int32_t n_vi
                     c->sum_ms[5] += ms;
                     c->timed_frames += 1;
                 }
-                fill_stats(c, vs, 1);
+                fill_stats(c, vs, c->graph_kernels);
                 return SPL_OK;
             }
             // a list outgrew its captured capacity: clear and render eagerly

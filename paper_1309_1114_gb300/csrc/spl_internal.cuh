@@ -56,6 +56,10 @@ struct FrameConst {
     long long rec_base;        // first record: record = rec_base + particle id
 };
 
+// Kernels launched by this host thread: every launch site adds one, and a
+// render reports the difference across its own launches.
+extern thread_local long long g_launches;
+
 // A batch of views rendered together: one particle set, nviews cameras.
 // Per-view constants live in device memory; the tile side is common.
 constexpr int kMaxViews = 64;

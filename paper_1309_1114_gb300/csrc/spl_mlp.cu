@@ -115,12 +115,14 @@ void launch_mlp_forward(const float *theta, const float *x, int64_t B, float *y,
     int64_t blocks = (B + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     mlp_forward_kernel<<<(unsigned)blocks, 256, 0, s>>>(theta, x, B, y);
+    ++g_launches;
 }
 
 void launch_mlp_loss_grad(const float *theta, const float *x, const float *t, int64_t B,
                           float *work, float *grad, float *loss, cudaStream_t s) {
     float *dz = work, *h = dz + B * kHid, *dy = h + B * kHid, *lpart = dy + B;
     mlp_backprop_kernel<<<kBackpropBlocks, 256, 0, s>>>(theta, x, t, B, dz, h, dy, lpart);
+    ++g_launches;
     mlp_reduce_kernel<<<(kNParam + 1 + 255) / 256, 256, 0, s>>>(x, dz, h, dy, B, lpart,
                                                                   kBackpropBlocks, grad, loss);
 }

@@ -374,6 +374,7 @@ void launch_raster(const Views &vs, const RasterArgs &a, int attr, cudaStream_t 
         if (rgb) raster_kernel<0, true><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
         else raster_kernel<0, false><<<(unsigned)blocks, 256, 0, s>>>(vs, a);
     }
+    ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -417,6 +418,7 @@ __global__ void __launch_bounds__(256) large_tiles_kernel(Views vs, BinArgs a) {
 void launch_count_large(const Views &vs, const BinArgs &a, int sms, cudaStream_t s) {
     if (vs.n <= 0) return;
     large_tiles_kernel<0><<<sms * 2, 256, 0, s>>>(vs, a);
+    ++g_launches;
 }
 
 __global__ void slot_sum_kernel(int m, const int *counts, int *ovf) {
@@ -478,19 +480,28 @@ __global__ void __launch_bounds__(1024) scan_kernel(int m, const int *in, OT *ou
 void launch_scan(int m, const int *in, long long *out, long long *cursor, int nseg,
                  long long *seg_totals, cudaStream_t s) {
     scan_kernel<long long><<<1, 1024, 0, s>>>(m, in, out, cursor, nseg, seg_totals);
+    ++g_launches;
 }
 
 void launch_scan(int m, const int *in, int *out, int *cursor, int nseg, int *seg_totals,
                  cudaStream_t s) {
     scan_kernel<int><<<1, 1024, 0, s>>>(m, in, out, cursor, nseg, seg_totals);
+    ++g_launches;
 }
 
 void launch_slot_offsets(int m, int *counts, int *ovf, long long *offsets, long long *cursor,
                          long long *total, cudaStream_t s) {
     const int grid = (m + 255) / 256 < 1024 ? (m + 255) / 256 : 1024;
-    if (grid > 0) slot_sum_kernel<<<grid, 256, 0, s>>>(m, counts, ovf);
+    if (grid > 0) {
+        slot_sum_kernel<<<grid, 256, 0, s>>>(m, counts, ovf);
+        ++g_launches;
+    }
     scan_kernel<long long><<<1, 1024, 0, s>>>(m, ovf, offsets, nullptr, 1, total);
-    if (grid > 0) slot_cursor_kernel<<<grid, 256, 0, s>>>(m, counts, offsets, cursor);
+    ++g_launches;
+    if (grid > 0) {
+        slot_cursor_kernel<<<grid, 256, 0, s>>>(m, counts, offsets, cursor);
+        ++g_launches;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -537,6 +548,7 @@ void launch_item_counts(const Views &vs, const long long *offsets, int *item_cou
                         cudaStream_t s) {
     const int blocks = (vs.total_tiles + 255) / 256;
     item_count_kernel<<<blocks, 256, 0, s>>>(vs, offsets, item_counts, st);
+    ++g_launches;
 }
 
 __device__ __forceinline__ void put_item(WorkItem *items, int cap, int pos, WorkItem w, DevStats *st) {
@@ -577,6 +589,7 @@ void launch_fill_items(const Views &vs, const long long *offsets, const int *ite
                        WorkItem *items, int items_cap, DevStats *st, cudaStream_t s) {
     const int blocks = (vs.total_tiles + 255) / 256;
     fill_items_kernel<<<blocks, 256, 0, s>>>(vs, offsets, item_offsets, items, items_cap, st);
+    ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -663,7 +676,9 @@ void launch_scatter(const Views &vs, const BinArgs &a, int sms, cudaStream_t s) 
     const size_t smem = (size_t)kHash * (sizeof(long long) + 2 * sizeof(int));
     cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     scatter_kernel<<<(unsigned)blocks, 256, smem, s>>>(vs, a);
+    ++g_launches;
     large_tiles_kernel<1><<<sms * 2, 256, 0, s>>>(vs, a);
+    ++g_launches;
 }
 
 // ---------------------------------------------------------------------------
@@ -712,6 +727,7 @@ void launch_count_work(const FrameConst &fc, const float4 *rec0, const float4 *r
     int64_t blocks = (n + 255) / 256;
     blocks = blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8;
     count_work_kernel<<<(unsigned)blocks, 256, 0, s>>>(fc, rec0, rec1, n, work);
+    ++g_launches;
 }
 
 }  // namespace spl

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(256) item_features_kernel(Views vs, TileArgs a
 void launch_item_features(const Views &vs, const TileArgs &a, float area_scale, int max_sample,
                           float *feat, int *n_entries, int sms, cudaStream_t s) {
     item_features_kernel<<<sms * 4, 256, 0, s>>>(vs, a, area_scale, max_sample, feat, n_entries);
+    ++g_launches;
 }
 
 // Entries of every item only (what the count heuristic needs): a segment's
@@ -120,6 +121,7 @@ __global__ void item_entries_kernel(Views vs, TileArgs a, int *n_entries) {
 void launch_item_entries(const Views &vs, const TileArgs &a, int *n_entries, int sms,
                          cudaStream_t s) {
     item_entries_kernel<<<sms * 4, 256, 0, s>>>(vs, a, n_entries);
+    ++g_launches;
 }
 
 // Predicted log-cycles of every item: the network when theta is given, else
@@ -158,6 +160,7 @@ void launch_item_cost(const float *feat, const int *n_entries, const float *thet
                       const float *heur, int items_cap, const DevStats *st, float *cost,
                       cudaStream_t s) {
     item_cost_kernel<<<256, 256, 0, s>>>(feat, n_entries, theta, heur, items_cap, st, cost);
+    ++g_launches;
 }
 
 // Longest first: bucket b holds predicted log-cycles in (25 - (b+1)/12.8, 25 - b/12.8].
@@ -207,8 +210,11 @@ void launch_order_items(const float *cost, int items_cap, DevStats *st, int *his
                         cudaStream_t s) {
     cudaMemsetAsync(hist, 0, sizeof(int) * 512, s);
     order_count_kernel<<<256, 256, 0, s>>>(cost, items_cap, st, hist);
+    ++g_launches;
     order_scan_kernel<<<1, 64, 0, s>>>(hist);
+    ++g_launches;
     order_place_kernel<<<256, 256, 0, s>>>(cost, items_cap, st, hist, order);
+    ++g_launches;
 }
 
 __global__ void log_cycles_kernel(const long long *cycles, int64_t n, float *logc) {
@@ -220,6 +226,7 @@ __global__ void log_cycles_kernel(const long long *cycles, int64_t n, float *log
 void launch_log_cycles(const long long *cycles, int64_t n, float *logc, cudaStream_t s) {
     if (n <= 0) return;
     log_cycles_kernel<<<256, 256, 0, s>>>(cycles, n, logc);
+    ++g_launches;
 }
 
 }  // namespace spl

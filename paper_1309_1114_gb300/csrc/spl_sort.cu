@@ -174,8 +174,10 @@ int64_t radix_scratch_ints(int64_t n) {
 static void scan_digits(int m, const int *in, int *out, int *part, int *pbase, cudaStream_t s) {
     const int np = scan_parts(m);
     scan_reduce_kernel<<<np, kScanThreads, 0, s>>>(in, m, part);
+    ++g_launches;
     launch_scan(np, part, pbase, nullptr, 0, nullptr, s);
     scan_apply_kernel<<<np, kScanThreads, 0, s>>>(in, m, pbase, np, out);
+    ++g_launches;
 }
 
 // Sorts keys[0, n) by the 8-bit digits at the given shifts (least
@@ -190,8 +192,10 @@ unsigned long long *launch_radix_sort(unsigned long long *keys, unsigned long lo
     unsigned long long *a = keys, *b = tmp;
     for (int p = 0; p < npasses; ++p) {
         radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(a, n, shifts[p], cnt, nb);
+        ++g_launches;
         scan_digits(m, cnt, bases, part, pbase, s);
         radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(a, b, n, shifts[p], bases, nb);
+        ++g_launches;
         unsigned long long *t = a;
         a = b;
         b = t;
@@ -271,19 +275,23 @@ void launch_depth_order(const float4 *rec1, const float2 *rec2, int64_t n, unsig
                         cudaStream_t s) {
     if (n <= 0 || total <= 0) return;
     depth_keys_kernel<<<sms * 8, 256, 0, s>>>(rec1, rec2, n, pkeys);
+    ++g_launches;
     int shifts[8], np = 0;
     const int idb = bits_for((unsigned long long)(n - 1));
     for (int sh = 0; sh < idb; sh += 8) shifts[np++] = sh;
     for (int sh = 32; sh < 64; sh += 8) shifts[np++] = sh;
     unsigned long long *ps = launch_radix_sort(pkeys, ptmp, n, shifts, np, hist, s);
     rank_kernel<<<sms * 8, 256, 0, s>>>(ps, n, rank);
+    ++g_launches;
     entry_keys_kernel<<<sms * 8, 256, 0, s>>>(entries, off, ntiles, rank, ekeys);
+    ++g_launches;
     np = 0;
     for (int sh = 0; sh < idb; sh += 8) shifts[np++] = sh;
     const int tb = bits_for((unsigned long long)(ntiles - 1));
     for (int sh = 32; sh < 32 + tb; sh += 8) shifts[np++] = sh;
     unsigned long long *es = launch_radix_sort(ekeys, etmp, total, shifts, np, hist, s);
     entry_store_kernel<<<sms * 8, 256, 0, s>>>(es, off, ntiles, ps, entries);
+    ++g_launches;
 }
 
 }  // namespace spl

@@ -510,6 +510,7 @@ static void launch_items_t(const Views &vs, const TileArgs &a, int sms, cudaStre
     cudaFuncSetAttribute(item_kernel<T, LARGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)bytes);
     item_kernel<T, LARGE><<<sms * min_ctas<T>(), kTileThreads, bytes, s>>>(vs, a);
+    ++g_launches;
 }
 
 template <bool LARGE>
@@ -542,6 +543,7 @@ void launch_epilogue_ea(float *image, int64_t nvals, int sms, cudaStream_t s) {
     int64_t blocks = (nvals + 255) / 256;
     blocks = blocks < (int64_t)sms * 4 ? blocks : (int64_t)sms * 4;
     epilogue_ea_kernel<<<(unsigned)blocks, 256, 0, s>>>(image, nvals);
+    ++g_launches;
 }
 
 // Grid-stride over every pixel value of every view (blockIdx.y = view).
@@ -800,9 +802,12 @@ static void launch_absorb_t(const Views &vs, const TileArgs &a, const int *item_
                             cudaStream_t s) {
     constexpr size_t bytes = absorb_smem_bytes<T>();
     absorb_kernel<T><<<sms * 2, kTileThreads, bytes, s>>>(vs, a);
+    ++g_launches;
     const int grid = vs.total_tiles < sms * 8 ? vs.total_tiles : sms * 8;
-    if (grid > 0)
+    if (grid > 0) {
         absorb_combine_kernel<T><<<grid, 256, 0, s>>>(vs, item_offsets, a.partial, a.images);
+        ++g_launches;
+    }
 }
 
 void launch_absorb_pass(const Views &vs, const TileArgs &a, const int *item_offsets, int sms,
@@ -828,10 +833,12 @@ __global__ void views_pointwise_kernel(Views vs, float *const *images) {
 
 void launch_zero_images(const Views &vs, float *const *images, int sms, cudaStream_t s) {
     views_pointwise_kernel<false><<<dim3(sms * 2, vs.nviews), 256, 0, s>>>(vs, images);
+    ++g_launches;
 }
 
 void launch_epilogue_views(const Views &vs, float *const *images, int sms, cudaStream_t s) {
     views_pointwise_kernel<true><<<dim3(sms * 2, vs.nviews), 256, 0, s>>>(vs, images);
+    ++g_launches;
 }
 
 }  // namespace spl
