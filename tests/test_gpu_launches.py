@@ -51,7 +51,8 @@ def test_reported_launches_match_the_profiler(rnd, torch_cuda, params):
     if not names:
         pytest.skip("the profiler recorded no kernels on this machine")
     st = rnd.stats()
-    assert st["n_large"] > 0
+    if params.get("mode") != 2:        # the absorbing path keeps one depth-sorted list per tile
+        assert st["n_large"] > 0
     assert st["launches"] == len(names), names
     rnd.set_params()
 
