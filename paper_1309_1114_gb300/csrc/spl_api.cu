@@ -488,6 +488,7 @@ static FrameConst make_frame(const spl_ctx *c, const spl_camera &cam) {
     fc.width = cam.width;
     fc.height = cam.height;
     fc.tile = q.tile_px;
+    fc.tile_shift = q.tile_px == 16 ? 4 : (q.tile_px == 32 ? 5 : 6);
     fc.ntx = (cam.width + q.tile_px - 1) / q.tile_px;
     fc.nty = (cam.height + q.tile_px - 1) / q.tile_px;
     fc.ntiles = fc.ntx * fc.nty;

@@ -47,12 +47,19 @@ __device__ __forceinline__ bool splat_box(const FrameConst &fc, float4 r0, float
     return b.i0 <= b.i1 && b.j0 <= b.j1;
 }
 
-// Does the disc (with the same margin) reach any pixel centre of tile (tx, ty)?
-__device__ __forceinline__ bool disc_meets_tile(const FrameConst &fc, float4 r0, float r2, int tx,
-                                                int ty) {
-    const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
+// Squared reach of a disc in the tile tests: the radius with the margin of
+// splat_box.
+__device__ __forceinline__ float disc_reach2(float r2) {
     const float r = sqrtf(r2);
     const float m = r + 1e-3f + 1e-6f * r;
+    return m * m;
+}
+
+// Does the disc (reach2 = disc_reach2(r^2)) reach any pixel centre of tile
+// (tx, ty)?
+__device__ __forceinline__ bool disc_meets_tile(const FrameConst &fc, float4 r0, float reach2, int tx,
+                                                int ty) {
+    const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
     // tile pixel-centre rectangle, relative to (xi, yi)
     const float ax = (float)(tx * fc.tile - xi) + 0.5f;
     const float bx = (float)(min((tx + 1) * fc.tile, fc.width) - 1 - xi) + 0.5f;
@@ -60,7 +67,7 @@ __device__ __forceinline__ bool disc_meets_tile(const FrameConst &fc, float4 r0,
     const float by = (float)(min((ty + 1) * fc.tile, fc.height) - 1 - yi) + 0.5f;
     const float dx = fminf(fmaxf(r0.y, ax), bx) - r0.y;
     const float dy = fminf(fmaxf(r0.z, ay), by) - r0.z;
-    return dx * dx + dy * dy <= m * m;
+    return dx * dx + dy * dy <= reach2;
 }
 
 // exp(-d2/sigma^2) = 2^(-kq d2) with the hardware exp2 (PTX ex2.approx.ftz.f32,

@@ -46,6 +46,7 @@ struct FrameConst {
     int npal;
     int width, height;
     int tile, ntx, nty, ntiles;
+    int tile_shift;            // log2(tile)
     // place of this view in a batch of views
     int view;                  // index in the batch
     int tile_base;             // first global tile: global tile = tile_base + local tile

@@ -44,10 +44,13 @@ __device__ __forceinline__ df df_mul(df a, df b) {
     e = fmaf(a.lo, b.hi, e);
     return fast_two_sum(p, e);
 }
-__device__ __forceinline__ df df_div(df a, df b) {
-    float q1 = a.hi / b.hi;
+// a / b given rb ~ 1 / b.hi (a few ulp suffice): the first quotient's
+// residual a - b q1 is formed in df and divided again, so the result keeps
+// df accuracy (relative error ~ eps(rb) * 2^-24 + 2^-44).
+__device__ __forceinline__ df df_div(df a, df b, float rb) {
+    float q1 = a.hi * rb;
     df r = df_add(a, df_neg(df_mul_f(b, q1)));
-    float q2 = r.hi / b.hi;
+    float q2 = r.hi * rb;
     return fast_two_sum(q1, q2);
 }
 
@@ -119,8 +122,9 @@ __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spa
     }
     // perspective projection
     const df f = {fc.fhi, fc.flo};
-    df xs = df_add({fc.half_w, 0.f}, df_mul(f, df_div(c[0], c[2])));
-    df ys = df_add({fc.half_h, 0.f}, df_neg(df_mul(f, df_div(c[1], c[2]))));
+    const float rz = 1.f / zc;
+    df xs = df_add({fc.half_w, 0.f}, df_mul(f, df_div(c[0], c[2], rz)));
+    df ys = df_add({fc.half_h, 0.f}, df_neg(df_mul(f, df_div(c[1], c[2], rz))));
     int xi, yi;
     float xf, yf;
     split_pos(xs, xi, xf);
@@ -162,15 +166,15 @@ __device__ __forceinline__ int raster_one(const FrameConst &fc, const float *spa
 // Large particles are handled by large_tiles_kernel.  In the absorption mode
 // points join the medium list, so that a tile's particles form one list that
 // can be ordered by depth.
-struct TileFoot { int list, tx0, ty0, bw, nbox, disc; };
+struct TileFoot { int list, tx0, ty0, bw, nbox, disc; float reach2; };
 
 __device__ __forceinline__ TileFoot tile_footprint(const FrameConst &fc, int cls, float4 r0, float4 r1) {
-    TileFoot f{-1, 0, 0, 1, 0, 0};
+    TileFoot f{-1, 0, 0, 1, 0, 0, 0.f};
     if (cls == CLS_POINT) {
         const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
         if (xi >= 0 && yi >= 0 && xi < fc.width && yi < fc.height) {
             f.list = fc.absorb ? L_MEDIUM : L_POINT;
-            f.tx0 = xi / fc.tile; f.ty0 = yi / fc.tile; f.nbox = 1;
+            f.tx0 = xi >> fc.tile_shift; f.ty0 = yi >> fc.tile_shift; f.nbox = 1;
         }
         return f;
     }
@@ -179,20 +183,30 @@ __device__ __forceinline__ TileFoot tile_footprint(const FrameConst &fc, int cls
     if (!splat_box(fc, r0, r1.x, b)) return f;
     f.list = cls == CLS_SMALL ? L_SMALL : L_MEDIUM;
     f.disc = 1;
-    f.tx0 = b.i0 / fc.tile;
-    f.ty0 = b.j0 / fc.tile;
-    f.bw = b.i1 / fc.tile - f.tx0 + 1;
-    f.nbox = f.bw * (b.j1 / fc.tile - f.ty0 + 1);
+    f.reach2 = disc_reach2(r1.x);
+    // the box is clamped to the image: non-negative pixel indices
+    f.tx0 = b.i0 >> fc.tile_shift;
+    f.ty0 = b.j0 >> fc.tile_shift;
+    f.bw = (b.i1 >> fc.tile_shift) - f.tx0 + 1;
+    f.nbox = f.bw * ((b.j1 >> fc.tile_shift) - f.ty0 + 1);
     return f;
 }
 
-// Slot (list * ntiles + tile) of the k-th tile of a footprint, or -1 when
-// k is past the box or the disc misses that tile.
-__device__ __forceinline__ int foot_slot(const FrameConst &fc, const TileFoot &f, int k, float4 r0,
-                                         float4 r1) {
-    if (k >= f.nbox) return -1;
-    const int tx = f.tx0 + k % f.bw, ty = f.ty0 + k / f.bw;
-    if (f.disc && !disc_meets_tile(fc, r0, r1.x, tx, ty)) return -1;
+// Walk over the tiles of a footprint, row by row: foot_next gives the slot
+// (list * ntiles + tile) of the current tile, or -1 when the walk is past the
+// box or the disc misses that tile, and steps to the next tile.
+struct FootWalk { int k, kx, ky; };
+
+__device__ __forceinline__ int foot_next(const FrameConst &fc, const TileFoot &f, float4 r0,
+                                         FootWalk &w) {
+    if (w.k >= f.nbox) return -1;
+    const int tx = f.tx0 + w.kx, ty = f.ty0 + w.ky;
+    ++w.k;
+    if (++w.kx == f.bw) {
+        w.kx = 0;
+        ++w.ky;
+    }
+    if (f.disc && !disc_meets_tile(fc, r0, f.reach2, tx, ty)) return -1;
     return f.list * fc.ntiles + ty * fc.ntx + tx;
 }
 
@@ -313,10 +327,11 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
                 a.rec1[rec] = r1;
                 if (a.rec2) a.rec2[rec] = q2;
             }
-            const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0, 0};
+            const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0, 0, 0.f};
             const int maxk = __reduce_max_sync(0xffffffffu, foot.nbox);
+            FootWalk walk{0, 0, 0};
             for (int k = 0; k < maxk; ++k) {
-                const int ls = foot_slot(fc, foot, k, r0, r1);
+                const int ls = foot_next(fc, foot, r0, walk);
                 count_round(ls >= 0 ? fc.slot_base + ls : -1, keys, vals, a.ovf, lane);
             }
             n_act += cls != CLS_INACTIVE;
@@ -394,12 +409,13 @@ __global__ void __launch_bounds__(256) large_tiles_kernel(Views vs, BinArgs a) {
         const float4 r1 = a.rec1[rec];
         PixBox b;
         if (!splat_box(fc, r0, r1.x, b)) continue;
-        const int tx0 = b.i0 / fc.tile, ty0 = b.j0 / fc.tile;
-        const int ntx = b.i1 / fc.tile - tx0 + 1;
-        const int nt = ntx * (b.j1 / fc.tile - ty0 + 1);
+        const int tx0 = b.i0 >> fc.tile_shift, ty0 = b.j0 >> fc.tile_shift;
+        const int ntx = (b.i1 >> fc.tile_shift) - tx0 + 1;
+        const int nt = ntx * ((b.j1 >> fc.tile_shift) - ty0 + 1);
+        const float reach2 = disc_reach2(r1.x);
         for (int k = lane; k < nt; k += 32) {
             const int tx = tx0 + k % ntx, ty = ty0 + k / ntx;
-            if (!disc_meets_tile(fc, r0, r1.x, tx, ty)) continue;
+            if (!disc_meets_tile(fc, r0, reach2, tx, ty)) continue;
             const int slot = fc.slot_base + L_LARGE * fc.ntiles + ty * fc.ntx + tx;
             if (MODE == 0) {
                 atomicAdd(&a.ovf[slot], 1);
@@ -601,10 +617,10 @@ __device__ __forceinline__ TileFoot load_foot(const FrameConst &fc, const BinArg
                                               bool valid, float4 &r0, float4 &r1) {
     r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
-    if (!valid) return TileFoot{-1, 0, 0, 1, 0, 0};
+    if (!valid) return TileFoot{-1, 0, 0, 1, 0, 0, 0.f};
     r1 = a.rec1[rec];
     const int cls = record_class(fc, r1.x);
-    if (cls == CLS_INACTIVE || cls == CLS_LARGE) return TileFoot{-1, 0, 0, 1, 0, 0};
+    if (cls == CLS_INACTIVE || cls == CLS_LARGE) return TileFoot{-1, 0, 0, 1, 0, 0, 0.f};
     r0 = a.rec0[rec];
     return tile_footprint(fc, cls, r0, r1);
 }
@@ -644,8 +660,9 @@ __global__ void __launch_bounds__(256) scatter_kernel(Views vs, BinArgs a) {
             float4 r0, r1;
             const TileFoot f = load_foot(fc, a, rec, i < c1, r0, r1);
             const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
+            FootWalk walk{0, 0, 0};
             for (int k = 0; k < maxk; ++k) {
-                const int ls = foot_slot(fc, f, k, r0, r1);
+                const int ls = foot_next(fc, f, r0, walk);
                 const int key = ls >= 0 ? fc.slot_base + ls : -1;
                 const unsigned m = __match_any_sync(0xffffffffu, key);
                 const int leader = __ffs(m) - 1;

@@ -10,8 +10,10 @@
 // Sec. 3.2.2 / Fig. 3).
 //
 // Inside an item every pixel of the tile has one owner thread: warp w owns a
-// band of T/8 rows, lane l owns the columns l (+32 for T = 64), and the
-// thread keeps its pixels' three channels in registers.  Then:
+// band of the tile (16 x 8 pixels for T = 32, 16 x 2 for T = 16, 64 x 8 for
+// T = 64), each lane a few pixels of it (T = 32: two adjacent columns of one
+// row pair; T = 16: one pixel; T = 64: two columns 32 apart, eight rows), and
+// the thread keeps its pixels' three channels in registers.  Then:
 //   - point particles (r <= r_sml, Sec. 4.1) add their emission to one pixel
 //     of a shared-memory copy of the tile; lanes of a warp that hit the same
 //     pixel are summed with warp shuffles first;
@@ -48,7 +50,12 @@ struct Shape {
     static constexpr int BW = T == 64 ? 64 : 16;
     static constexpr int BH = T * T / (8 * BW);
     static constexpr int NBX = T / BW;             // bands across the tile
-    static constexpr int LW = BW < 32 ? BW : 32;   // lanes along a band row
+    // lanes along a band row: 8 for T = 32, so that a lane's two columns
+    // share each row-pair load and the column table is read 16 bytes at a time
+    static constexpr int LW = T == 32 ? 8 : (BW < 32 ? BW : 32);
+    // a lane's columns: col + CSTEP k, k < CPL, col = band column + CMUL * (lane % LW)
+    static constexpr int CSTEP = T == 32 ? 1 : 32;
+    static constexpr int CMUL = T == 32 ? 2 : 1;
     static constexpr int G = 32 / LW;              // lane groups (rows split between them)
     static constexpr int CPL = BW / LW;            // columns per lane
     static constexpr int RPL = BH / G;             // rows per lane
@@ -273,7 +280,7 @@ __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp
     float wx[S::CPL], dxb[S::CPL];
 #pragma unroll
     for (int k = 0; k < S::CPL; ++k) {
-        const float2 v = wxp[col + 32 * k];
+        const float2 v = wxp[col + S::CSTEP * k];
         wx[k] = v.x;
         dxb[k] = v.y;
     }
@@ -290,8 +297,9 @@ __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp
     }
 }
 
-// The same two rows at a time: per row pair two 16-byte loads, two scalar
-// clips, one packed multiply and three packed FMAs (R, G, B of both rows).
+// The same two rows at a time: per row pair two 16-byte loads, and per
+// column two scalar clips, one packed multiply and three packed FMAs (R, G, B
+// of both rows).
 // rowp points at the particle's first-half row-pair table (see tabulate).
 template <int T>
 __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp, int col, int row0,
@@ -299,11 +307,21 @@ __device__ __forceinline__ void band_splat(const float2 *wxp, const float4 *rowp
     using S = Shape<T>;
     float dxb[S::CPL];
     f32x2 ww[S::CPL];
+    if constexpr (S::CSTEP == 1 && S::CPL == 2) {
+        // two adjacent columns in one 16-byte load (col is even, rows of the
+        // column table are 16-byte aligned)
+        const float4 v = *reinterpret_cast<const float4 *>(wxp + col);
+        ww[0] = pack2(v.x, v.x);
+        dxb[0] = v.y;
+        ww[1] = pack2(v.z, v.z);
+        dxb[1] = v.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < S::CPL; ++k) {
-        const float2 v = wxp[col + 32 * k];
-        ww[k] = pack2(v.x, v.x);
-        dxb[k] = v.y;
+        for (int k = 0; k < S::CPL; ++k) {
+            const float2 v = wxp[col + S::CSTEP * k];
+            ww[k] = pack2(v.x, v.x);
+            dxb[k] = v.y;
+        }
     }
     const ulonglong2 *ra_ = reinterpret_cast<const ulonglong2 *>(rowp) + row0 / 2;
     const ulonglong2 *rb_ = ra_ + S::P * (T / 2);
@@ -331,6 +349,7 @@ __host__ __device__ constexpr size_t table_bytes() {
     using S = Shape<T>;
     return sizeof(float4) * S::P * T + sizeof(float2) * S::P * S::WXS;
 }
+static_assert(Shape<32>::WXS * sizeof(float2) % 16 == 0, "16-byte column-table rows");
 static_assert(table_bytes<16>() >= sizeof(float) * 3 * 16 * 16, "shared tile fits the tables");
 static_assert(table_bytes<32>() >= sizeof(float) * 3 * 32 * 32, "shared tile fits the tables");
 static_assert(table_bytes<64>() >= sizeof(float) * 3 * 64 * 64, "shared tile fits the tables");
@@ -392,7 +411,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
         } else {
             lb2 = w.start; le2 = w.end;      // medium (tile pass) or large (large pass)
         }
-        const int col = (warp % S::NBX) * S::BW + lane % S::LW;
+        const int col = (warp % S::NBX) * S::BW + (lane % S::LW) * S::CMUL;
         const int row0 = (warp / S::NBX) * S::BH + (lane / S::LW) * S::RPL;
         Acc<T> acc;
         acc.zero();
@@ -484,7 +503,7 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
             const int row = row0 + q;
 #pragma unroll
             for (int k = 0; k < S::CPL; ++k) {
-                const int cx = col + 32 * k;
+                const int cx = col + S::CSTEP * k;
                 if (y0 + row >= fc.height || x0 + cx >= fc.width) continue;
                 float *dst = image + 3 * ((int64_t)(y0 + row) * fc.width + x0 + cx);
 #pragma unroll
@@ -691,7 +710,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) absorb_kernel(Views vs, TileA
             lb = a.offsets[fc.slot_base + L_MEDIUM * fc.ntiles + tile];
             le = a.offsets[fc.slot_base + L_MEDIUM * fc.ntiles + tile + 1];
         }
-        const int col = (warp % S::NBX) * S::BW + lane % S::LW;
+        const int col = (warp % S::NBX) * S::BW + (lane % S::LW) * S::CMUL;
         const int row0 = (warp / S::NBX) * S::BH + (lane / S::LW) * S::RPL;
         float Tr[S::RPL][S::CPL], C[S::RPL][S::CPL][3];
 #pragma unroll
@@ -723,7 +742,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) absorb_kernel(Views vs, TileA
                 float wx[S::CPL], dxb[S::CPL];
 #pragma unroll
                 for (int k = 0; k < S::CPL; ++k) {
-                    const float2 v = swx[p][col + 32 * k];
+                    const float2 v = swx[p][col + S::CSTEP * k];
                     wx[k] = v.x;
                     dxb[k] = v.y;
                 }
@@ -750,7 +769,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) absorb_kernel(Views vs, TileA
             const int row = row0 + q;
 #pragma unroll
             for (int k = 0; k < S::CPL; ++k) {
-                const int cx = col + 32 * k;
+                const int cx = col + S::CSTEP * k;
                 if (y0 + row >= fc.height || x0 + cx >= fc.width) continue;
                 if (list < 0) {
                     float *dst = image + 3 * ((int64_t)(y0 + row) * fc.width + x0 + cx);

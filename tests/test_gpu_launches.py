@@ -25,15 +25,20 @@ def rnd(torch_cuda):
 
 
 def profiled_kernels(torch, fn):
-    """Kernels launched while fn runs, as the profiler records them."""
+    """Kernels launched while fn runs, as the profiler records them (the
+    first session of a process may come back empty while the profiling
+    interface starts: one retry)."""
     from torch.profiler import ProfilerActivity, profile
-    torch.cuda.synchronize()
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
-        fn()
+    for _ in range(2):
         torch.cuda.synchronize()
-    names = [e.name for e in prof.events()
-             if e.device_type == torch.autograd.DeviceType.CUDA and "emcpy" not in e.name
-             and "emset" not in e.name]
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events()
+                 if e.device_type == torch.autograd.DeviceType.CUDA and "emcpy" not in e.name
+                 and "emset" not in e.name]
+        if names:
+            return names
     return names
 
 
