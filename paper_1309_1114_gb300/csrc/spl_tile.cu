@@ -212,12 +212,8 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
     const float B = __fdividef(1048576.f, r2);
     const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
     const float xh = 0.5f - r0.y, yh = 0.5f - r0.z;
-    // the particle's box in tile coordinates (conservative by 1e-3 px)
+    // the disc's radius for the band test (conservative by 1e-3 px)
     const float r = r2 * rsqrtf(r2) + 1e-3f;   // approximate: far inside the margin
-    const int ilo = xi - x0 + (int)ceilf(fmaxf(r0.y - 0.5f - r, -1e6f));
-    const int ihi = xi - x0 + (int)floorf(fminf(r0.y - 0.5f + r, 1e6f));
-    const int jlo = yi - y0 + (int)ceilf(fmaxf(r0.z - 0.5f - r, -1e6f));
-    const int jhi = yi - y0 + (int)floorf(fminf(r0.z - 0.5f + r, 1e6f));
     // offsets of this thread's first column and row from the particle centre;
     // the others follow by adding small integers (exact in FP32)
     const float dxq = ((float)(x0 - xi) + xh) + (float)q;
@@ -252,14 +248,14 @@ __device__ __forceinline__ void tabulate(const float4 *st0, const float4 *st1, i
         }
     }
     // row band q: columns [bx BW, bx BW + BW), rows [by BH, by BH + BH); the
-    // disc (with the box's margin) must reach the band's nearest pixel centre
+    // disc (with a margin) must reach the rectangle of the band's pixel
+    // centres.  A superset of the bands that hold a covered pixel: a band
+    // visited in vain adds clipped zeros.
     const int bx0 = (q % S::NBX) * S::BW, by0 = (q / S::NBX) * S::BH;
-    const int bx1 = bx0 + S::BW - 1, by1 = by0 + S::BH - 1;
     const float ax = (float)(x0 + bx0 - xi) + xh, ay = (float)(y0 + by0 - yi) + yh;
     const float nx = fmaxf(ax, fminf(0.f, ax + (float)(S::BW - 1)));
     const float ny = fmaxf(ay, fminf(0.f, ay + (float)(S::BH - 1)));
-    const bool hit = valid && jhi >= by0 && jlo <= by1 && ihi >= bx0 && ilo <= bx1 &&
-                     nx * nx + ny * ny <= r * r;
+    const bool hit = valid && nx * nx + ny * ny <= r * r;
     // lane 8j + q holds particle 4w + j of warp w and band q: lane q < 8 gathers
     // its band's four bits and sets them with one atomic
     const unsigned hb = __ballot_sync(0xffffffffu, hit);
