@@ -20,11 +20,15 @@ the header comment of ``splotch_oracle.c``.  Parity status per function:
   particle dict; ``par["log"]`` bit 1 = log10 of I, bit 2 = log10 of s):
   pinned by a hand value, the constant-palette equivalence, channel
   separation and exact powers of ten in ``tests/test_oracle_colour.py``.
-* ``render`` / ``render_bruteforce`` with ``mode = 2`` (Eq. 1 with independent
-  emission and absorption over depth-ordered particles): pinned by hand-worked
-  two-particle cases (both orders, equal depths), the E = A special case, the
-  optically thin and opaque limits, input-order invariance and the pixel-major
-  brute force in ``tests/test_oracle_absorb.py``.
+* ``render`` / ``render_bruteforce`` / ``render_pixels`` with ``mode = 2`` (Eq. 1
+  with independent emission and absorption over particles in FP64 depth order):
+  pinned by hand-worked two-particle cases (both orders, equal depths, depths
+  closer than one FP32 ulp), the E = A special case, the optically thin and
+  opaque limits, input-order invariance, the pixel-major brute force and the
+  full image at every pixel in ``tests/test_oracle_absorb.py``.
+* ``ambiguity`` in mode 2 (near-tie mass of particles within two FP32 ulps in
+  depth) and ``render_pixels(..., with_mass=True)``: pinned by the near-tie
+  cases and by the full-image mass at every pixel in the same file.
 """
 from __future__ import annotations
 
@@ -77,7 +81,7 @@ def _load():
             parts = [C.c_long, fp, fp, fp, fp, fp, fp, fp, C.c_int, cam, par]
             lib.orc_project.argtypes = parts + [dp, dp, dp, dp, dp, ip]
             lib.orc_render.argtypes = parts + [dp, C.c_int]
-            lib.orc_render_pixels.argtypes = parts + [C.c_long, ip, ip, dp, C.c_int]
+            lib.orc_render_pixels.argtypes = parts + [C.c_long, ip, ip, dp, C.c_void_p, C.c_int]
             lib.orc_render_bruteforce.argtypes = parts + [dp]
             lib.orc_ambiguity.argtypes = parts + [dp, lp]
             lib.orc_view_info.argtypes = [cam, dp]
@@ -188,18 +192,22 @@ def render(parts, palette, cam, par=None, nthreads: int = 1) -> np.ndarray:
     return img
 
 
-def render_pixels(parts, palette, cam, par, px, py, nthreads: int = 1) -> np.ndarray:
-    """Values (k x 3) of the pixels (px[k], py[k]), pixel-major."""
+def render_pixels(parts, palette, cam, par, px, py, nthreads: int = 1, with_mass: bool = False):
+    """Values (k x 3) of the pixels (px[k], py[k]), pixel-major; with_mass also
+    returns their ambiguity mass (k x 3), equal to ``ambiguity``'s there.  Mode 2
+    sorts every pixel's particles by FP64 depth and crosses them (Eq. 1)."""
     lib = _load()
     n, keep, args = _args(parts, palette, cam, par)
     px = np.ascontiguousarray(px, dtype=np.int32)
     py = np.ascontiguousarray(py, dtype=np.int32)
     out = np.zeros((px.size, 3))
+    B = np.zeros((px.size, 3)) if with_mass else None
     rc = lib.orc_render_pixels(*args, px.size, _ptr(px, C.c_int), _ptr(py, C.c_int),
-                               _ptr(out, C.c_double), int(nthreads))
+                               _ptr(out, C.c_double), None if B is None else B.ctypes.data,
+                               int(nthreads))
     if rc:
         raise ValueError(f"orc_render_pixels failed ({rc})")
-    return out
+    return (out, B) if with_mass else out
 
 
 def render_bruteforce(parts, palette, cam, par=None) -> np.ndarray:

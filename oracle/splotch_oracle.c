@@ -351,65 +351,6 @@ static void pixel_term(const orc_rec *o, long i, long j, double *acc) {
     }
 }
 
-/* Selected pixels, pixel-major: out[3*k..] = value of pixel (px[k], py[k]).
- * Particles are projected once per chunk; threads own chunks and keep their
- * own partial sums, summed at the end. */
-int orc_render_pixels(long n, const float *x, const float *y, const float *z,
-                      const float *h, const float *inten, const float *s,
-                      const float *pal, int npal, const orc_camera *cam,
-                      const orc_params *q, long npix, const int *px,
-                      const int *py, double *out, int nthreads) {
-    orc_view v;
-    if (npal < 1 || make_view(cam, &v)) return -1;
-    const long chunk = 16384;
-    long nchunks = (n + chunk - 1) / chunk;
-    memset(out, 0, sizeof(double) * 3 * npix);
-    if (nthreads < 1) nthreads = 1;
-    int nt = nthreads;
-#ifndef _OPENMP
-    nt = 1;
-#endif
-    double *part = (double *)calloc((size_t)nt * 3 * npix, sizeof(double));
-    if (!part) return -2;
-    int err = 0;
-#ifdef _OPENMP
-#pragma omp parallel num_threads(nt)
-#endif
-    {
-        int t = 0;
-#ifdef _OPENMP
-        t = omp_get_thread_num();
-#endif
-        orc_rec *rec = (orc_rec *)malloc(sizeof(orc_rec) * chunk);
-        if (!rec) {
-            err = 1;
-        } else {
-#ifdef _OPENMP
-#pragma omp for schedule(dynamic, 1)
-#endif
-            for (long c = 0; c < nchunks; ++c) {
-                long lo = c * chunk, hi = lo + chunk < n ? lo + chunk : n;
-                for (long p = lo; p < hi; ++p)
-                    project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p],
-                                inten[p], s[p], &rec[p - lo]);
-                for (long k = 0; k < npix; ++k) {
-                    double *acc = part + ((long)t * npix + k) * 3;
-                    for (long p = 0; p < hi - lo; ++p)
-                        pixel_term(&rec[p], px[k], py[k], acc);
-                }
-            }
-            free(rec);
-        }
-    }
-    for (int t = 0; t < nt; ++t)
-        for (long k = 0; k < 3 * npix; ++k) out[k] += part[(long)t * 3 * npix + k];
-    free(part);
-    if (err) return -2;
-    if (q->mode == 1)
-        for (long k = 0; k < 3 * npix; ++k) out[k] = -expm1(-out[k]);
-    return 0;
-}
-
 /* Whole image, pixel-major brute force (every pixel against every particle).
  * For tiny scenes only: it pins the particle-major loop's bounding box. */
 int orc_render_bruteforce(long n, const float *x, const float *y, const float *z,
@@ -452,9 +393,9 @@ int orc_render_bruteforce(long n, const float *x, const float *y, const float *z
  *   - a particle with A_p <= 0 (I_p = 0, or a non-positive logarithm of I)
  *     emits nothing and absorbs nothing;
  *   - the ray starts with I = 0 behind the farthest particle and ends at the
- *     observer: particles are taken in decreasing camera depth, the depth key
- *     being z_c rounded to float, equal keys in decreasing particle index (so
- *     that the ascending (key, index) order runs front to back);
+ *     observer: particles are taken in decreasing camera depth z_c (FP64),
+ *     equal depths in decreasing particle index (so that the ascending
+ *     (z_c, index) order runs front to back);
  *   - with a constant palette equal to `absorption` in every channel E_p = A_p,
  *     and the result is the E=A map 1 - exp(-S) of mode 1.
  * pixel_major = 0: particle-major over the sorted particles, an H*W*3 image
@@ -462,7 +403,7 @@ int orc_render_bruteforce(long n, const float *x, const float *y, const float *z
  * particles (the brute force of the tests).
  */
 typedef struct {
-    float key;
+    double key;
     long id;
 } orc_depth;
 
@@ -510,7 +451,7 @@ static int render_absorb(long n, const float *x, const float *y, const float *z,
     for (long p = 0; p < n; ++p) {
         project_one(v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &rec[p]);
         if (rec[p].cls != ORC_INACTIVE && q->absorption * rec[p].ib > 0.0) {
-            ord[m].key = (float)rec[p].zc;
+            ord[m].key = rec[p].zc;
             ord[m].id = p;
             ++m;
         }
@@ -613,8 +554,15 @@ static void ambiguity_one(const orc_view *v, const orc_params *q, const orc_rec 
     }
 }
 
+static int near_tie_mass(long n, const float *x, const float *y, const float *z,
+                         const float *h, const float *inten, const float *s, const float *pal,
+                         int npal, const orc_view *v, const orc_params *q, double *B);
+
 /* B image plus the number of particles whose class or point pixel is
- * ambiguous (clip-edge ambiguity is reported through B only). */
+ * ambiguous (clip-edge ambiguity is reported through B only).  In mode 2 B
+ * also holds the near-tie mass (near_tie_mass): contributions of particles
+ * whose depth lies within two FP32 ulps of another particle's that reaches
+ * the same pixel. */
 int orc_ambiguity(long n, const float *x, const float *y, const float *z,
                   const float *h, const float *inten, const float *s,
                   const float *pal, int npal, const orc_camera *cam,
@@ -642,6 +590,292 @@ int orc_ambiguity(long n, const float *x, const float *y, const float *z,
         ambiguity_one(&v, q, &o, B);
     }
     if (n_amb_particles) *n_amb_particles = cnt;
+    if (q->mode == 2) return near_tie_mass(n, x, y, z, h, inten, s, pal, npal, &v, q, B);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Selected pixels, pixel-major, with their ambiguity mass                 */
+/* ---------------------------------------------------------------------- */
+
+/* Ambiguity mass of one projected particle at pixel (i, j): the three rules
+ * of ambiguity_one evaluated at one pixel.  e3 is the magnitude per channel
+ * that a flipped contribution of weight 1 carries. */
+static void pixel_ambiguity(const orc_params *q, const orc_rec *o, const double *e3, long i,
+                            long j, double *B) {
+    if (o->cls == ORC_INACTIVE) return;
+    int class_amb = fabs(o->r - q->r_sml) < 1e-6 * q->r_sml;
+    if (o->cls == ORC_POINT || class_amb) {
+        double mx = floor(o->xs + 0.5), my = floor(o->ys + 0.5);
+        int ax = fabs(o->xs - mx) < 1e-5, ay = fabs(o->ys - my) < 1e-5;
+        int on_x = ax ? (i == (long)mx - 1 || i == (long)mx) : i == (long)floor(o->xs);
+        int on_y = ay ? (j == (long)my - 1 || j == (long)my) : j == (long)floor(o->ys);
+        if ((class_amb || ax || ay) && on_x && on_y)
+            for (int k = 0; k < 3; ++k) B[k] += fabs(e3[k]);
+    }
+    if (o->cls == ORC_SPLAT || class_amb) {
+        double band = 1e-5 * o->r + 1e-6, rr = o->r + band;
+        double dx = (i + 0.5) - o->xs, dy = (j + 0.5) - o->ys;
+        double d = sqrt(dx * dx + dy * dy);
+        if (class_amb ? d <= rr : fabs(d - o->r) < band) {
+            double w = exp(-(d * d) / (o->sigma * o->sigma));
+            for (int k = 0; k < 3; ++k) B[k] += fabs(e3[k]) * w;
+        }
+    }
+}
+
+/* Mode 2: two absorbing particles whose FP64 depths lie this close together
+ * (the smaller is at least the larger times 1 - 2^-22, i.e. within two FP32
+ * ulps) may be crossed in either order by a renderer whose depth key is a
+ * float.  The relation is monotone along sorted depths, so the particles
+ * near one particle form a contiguous run around it in depth order. */
+static int depth_near(double za, double zb) {
+    double lo = za < zb ? za : zb, hi = za < zb ? zb : za;
+    return lo >= hi * (1.0 - 0x1p-22);
+}
+
+/* Largest magnitude of a palette entry: in mode 2 a contribution tau = A w
+ * moves a pixel by at most tau * max(E/A) = brightness * I * w * pal_max. */
+static double palette_max(const float *pal, int npal) {
+    double m = 0.0;
+    for (long k = 0; k < 3L * npal; ++k) m = fmax(m, fabs((double)pal[k]));
+    return m;
+}
+
+/* Mode 2 near-tie mass of a whole image: a contribution of particle p to a
+ * pixel is ambiguous when another absorbing particle whose depth is near p's
+ * (depth_near) also reaches that pixel: swapping two such particles changes
+ * the pixel by at most g_1 g_2 |S_1 - S_2| <= the mass of either of them, and
+ * permuting a run of them by at most the sum of the run's masses. */
+static int near_tie_mass(long n, const float *x, const float *y, const float *z,
+                         const float *h, const float *inten, const float *s, const float *pal,
+                         int npal, const orc_view *v, const orc_params *q, double *B) {
+    double pal_max = palette_max(pal, npal);
+    orc_rec *rec = (orc_rec *)malloc(sizeof(orc_rec) * (n > 0 ? n : 1));
+    orc_depth *ord = (orc_depth *)malloc(sizeof(orc_depth) * (n > 0 ? n : 1));
+    if (!rec || !ord) {
+        free(rec);
+        free(ord);
+        return -2;
+    }
+    long m = 0;
+    for (long p = 0; p < n; ++p) {
+        project_one(v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &rec[p]);
+        if (rec[p].cls != ORC_INACTIVE && q->absorption * rec[p].ib > 0.0) {
+            ord[m].key = rec[p].zc;
+            ord[m].id = p;
+            ++m;
+        }
+    }
+    qsort(ord, (size_t)m, sizeof(orc_depth), cmp_back_to_front);
+    for (long k = 0; k < m; ++k) {
+        long a = k, b = k;
+        while (a > 0 && depth_near(ord[a - 1].key, ord[k].key)) --a;
+        while (b + 1 < m && depth_near(ord[b + 1].key, ord[k].key)) ++b;
+        if (a == b) continue;
+        const orc_rec *o = &rec[ord[k].id];
+        double e3[3] = {fabs(o->ib) * pal_max, fabs(o->ib) * pal_max, fabs(o->ib) * pal_max};
+        double i0, i1, j0, j1;
+        if (o->cls == ORC_POINT) {
+            i0 = i1 = floor(o->xs);
+            j0 = j1 = floor(o->ys);
+        } else {
+            i0 = ceil(o->xs - o->r - 0.5); i1 = floor(o->xs + o->r - 0.5);
+            j0 = ceil(o->ys - o->r - 0.5); j1 = floor(o->ys + o->r - 0.5);
+        }
+        if (i0 < 0.0) i0 = 0.0;
+        if (j0 < 0.0) j0 = 0.0;
+        if (i1 > v->w - 1) i1 = v->w - 1;
+        if (j1 > v->h - 1) j1 = v->h - 1;
+        for (long j = (long)j0; j <= (long)j1; ++j)
+            for (long i = (long)i0; i <= (long)i1; ++i) {
+                double w = pixel_weight(o, i, j);
+                if (!(w > 0.0)) continue;
+                int shared = 0;
+                for (long t = a; t <= b && !shared; ++t)
+                    if (t != k && pixel_weight(&rec[ord[t].id], i, j) > 0.0) shared = 1;
+                if (shared) add_mass(v, i, j, e3, w, B);
+            }
+    }
+    free(rec);
+    free(ord);
+    return 0;
+}
+
+/* One absorbing particle that reaches a selected pixel. */
+typedef struct {
+    double z, w;
+    long id;
+} orc_hit;
+
+static int cmp_hit_back_to_front(const void *pa, const void *pb) {
+    const orc_hit *a = (const orc_hit *)pa, *b = (const orc_hit *)pb;
+    if (a->z != b->z) return a->z > b->z ? -1 : 1;
+    if (a->id != b->id) return a->id > b->id ? -1 : 1;
+    return 0;
+}
+
+/* Mode 2 at selected pixels: every pixel collects the absorbing particles
+ * that reach it, sorts them from the farthest to the nearest (FP64 depth, then
+ * decreasing index) and crosses them one after the other -- the pixel-major
+ * branch of render_absorb, restricted to the selected pixels.  B (may be NULL)
+ * receives the ambiguity mass: the rules of pixel_ambiguity with the mode-2
+ * magnitude, plus the near-tie mass of near_tie_mass. */
+static int pixels_absorb(long n, const float *x, const float *y, const float *z,
+                         const float *h, const float *inten, const float *s, const float *pal,
+                         int npal, const orc_view *v, const orc_params *q, long npix,
+                         const int *px, const int *py, double *out, double *B, int nt) {
+    if (!(q->absorption > 0.0)) return -1;
+    double pal_max = palette_max(pal, npal);
+    const long chunk = 16384;
+    orc_rec *rec = (orc_rec *)malloc(sizeof(orc_rec) * chunk);
+    orc_hit **hits = (orc_hit **)calloc((size_t)(npix > 0 ? npix : 1), sizeof(orc_hit *));
+    long *cnt = (long *)calloc((size_t)(npix > 0 ? npix : 1), sizeof(long));
+    long *cap = (long *)calloc((size_t)(npix > 0 ? npix : 1), sizeof(long));
+    int err = 0;
+    if (!rec || !hits || !cnt || !cap) err = 1;
+    memset(out, 0, sizeof(double) * 3 * npix);
+    if (B) memset(B, 0, sizeof(double) * 3 * npix);
+    for (long lo = 0; lo < n && !err; lo += chunk) {
+        long hi = lo + chunk < n ? lo + chunk : n;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt)
+#endif
+        for (long p = lo; p < hi; ++p)
+            project_one(v, q, pal, npal, p, x[p], y[p], z[p], h[p], inten[p], s[p], &rec[p - lo]);
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 8) reduction(| : err)
+#endif
+        for (long k = 0; k < npix; ++k) {
+            for (long p = lo; p < hi; ++p) {
+                const orc_rec *o = &rec[p - lo];
+                if (o->cls == ORC_INACTIVE) continue;
+                if (B) {
+                    double e3[3] = {fabs(o->ib) * pal_max, fabs(o->ib) * pal_max,
+                                    fabs(o->ib) * pal_max};
+                    pixel_ambiguity(q, o, e3, px[k], py[k], B + 3 * k);
+                }
+                if (!(q->absorption * o->ib > 0.0)) continue;
+                double w = pixel_weight(o, px[k], py[k]);
+                if (!(w > 0.0)) continue;
+                if (cnt[k] == cap[k]) {
+                    long nc = cap[k] ? 2 * cap[k] : 64;
+                    orc_hit *g = (orc_hit *)realloc(hits[k], sizeof(orc_hit) * nc);
+                    if (!g) {
+                        err |= 1;
+                        break;
+                    }
+                    hits[k] = g;
+                    cap[k] = nc;
+                }
+                hits[k][cnt[k]].z = o->zc;
+                hits[k][cnt[k]].w = w;
+                hits[k][cnt[k]].id = p;
+                cnt[k]++;
+            }
+        }
+    }
+    if (!err) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+#endif
+        for (long k = 0; k < npix; ++k) {
+            orc_hit *hk = hits[k];
+            long c = cnt[k];
+            qsort(hk, (size_t)c, sizeof(orc_hit), cmp_hit_back_to_front);
+            double *I = out + 3 * k;
+            for (long m = 0; m < c; ++m) {
+                long id = hk[m].id;
+                orc_rec o;
+                project_one(v, q, pal, npal, id, x[id], y[id], z[id], h[id], inten[id], s[id], &o);
+                cross_particle(&o, q, hk[m].w, I);
+                if (B && ((m > 0 && depth_near(hk[m - 1].z, hk[m].z)) ||
+                          (m + 1 < c && depth_near(hk[m + 1].z, hk[m].z))))
+                    for (int ch = 0; ch < 3; ++ch) B[3 * k + ch] += fabs(o.ib) * pal_max * hk[m].w;
+            }
+        }
+    }
+    if (hits)
+        for (long k = 0; k < npix; ++k) free(hits[k]);
+    free(hits);
+    free(cnt);
+    free(cap);
+    free(rec);
+    return err ? -2 : 0;
+}
+
+/* Selected pixels, pixel-major: out[3*k..] = value of pixel (px[k], py[k]),
+ * and (B not NULL) B[3*k..] = its ambiguity mass, the same as orc_ambiguity's
+ * at that pixel.  Modes 0 and 1: particles are projected once per chunk;
+ * threads own chunks and keep their own partial sums, summed at the end.
+ * Mode 2: pixels_absorb. */
+int orc_render_pixels(long n, const float *x, const float *y, const float *z,
+                      const float *h, const float *inten, const float *s,
+                      const float *pal, int npal, const orc_camera *cam,
+                      const orc_params *q, long npix, const int *px,
+                      const int *py, double *out, double *B, int nthreads) {
+    orc_view v;
+    if (npal < 1 || make_view(cam, &v)) return -1;
+    for (long k = 0; k < npix; ++k)
+        if (px[k] < 0 || py[k] < 0 || px[k] >= v.w || py[k] >= v.h) return -1;
+    if (nthreads < 1) nthreads = 1;
+    int nt = nthreads;
+#ifndef _OPENMP
+    nt = 1;
+#endif
+    if (q->mode == 2)
+        return pixels_absorb(n, x, y, z, h, inten, s, pal, npal, &v, q, npix, px, py, out, B, nt);
+    const long chunk = 16384;
+    long nchunks = (n + chunk - 1) / chunk;
+    memset(out, 0, sizeof(double) * 3 * npix);
+    if (B) memset(B, 0, sizeof(double) * 3 * npix);
+    double *part = (double *)calloc((size_t)nt * 3 * npix * (B ? 2 : 1) + 1, sizeof(double));
+    if (!part) return -2;
+    double *bpart = B ? part + (size_t)nt * 3 * npix : NULL;
+    int err = 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        orc_rec *rec = (orc_rec *)malloc(sizeof(orc_rec) * chunk);
+        if (!rec) {
+            err = 1;
+        } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+            for (long c = 0; c < nchunks; ++c) {
+                long lo = c * chunk, hi = lo + chunk < n ? lo + chunk : n;
+                for (long p = lo; p < hi; ++p)
+                    project_one(&v, q, pal, npal, p, x[p], y[p], z[p], h[p],
+                                inten[p], s[p], &rec[p - lo]);
+                for (long k = 0; k < npix; ++k) {
+                    double *acc = part + ((long)t * npix + k) * 3;
+                    for (long p = 0; p < hi - lo; ++p)
+                        pixel_term(&rec[p], px[k], py[k], acc);
+                    if (bpart) {
+                        double *bacc = bpart + ((long)t * npix + k) * 3;
+                        for (long p = 0; p < hi - lo; ++p)
+                            pixel_ambiguity(q, &rec[p], rec[p].e, px[k], py[k], bacc);
+                    }
+                }
+            }
+            free(rec);
+        }
+    }
+    for (int t = 0; t < nt; ++t)
+        for (long k = 0; k < 3 * npix; ++k) {
+            out[k] += part[(long)t * 3 * npix + k];
+            if (B) B[k] += bpart[(long)t * 3 * npix + k];
+        }
+    free(part);
+    if (err) return -2;
+    if (q->mode == 1)
+        for (long k = 0; k < 3 * npix; ++k) out[k] = -expm1(-out[k]);
     return 0;
 }
 

@@ -7,6 +7,12 @@ of each other, both orders, and equal depths), against the E = A special case
 (whose solution 1 - exp(-S) is order-free), against the optically thin limit
 (small absorption gives the additive sum), against opacity (large absorption
 gives the nearest source term), and against the pixel-major brute force.
+Particles are ordered by their FP64 depth (two depths closer than one FP32 ulp
+are still crossed in their true order); the ambiguity mass gains every
+contribution whose depth lies within two FP32 ulps of another contribution to
+the same pixel, which bounds what a renderer ordering by an FP32 depth key may
+legitimately do differently.  The sampled-pixel oracle equals the full image
+(values and mass) at every pixel in every mode.
 """
 import math
 
@@ -137,3 +143,103 @@ def test_absorption_must_be_positive():
     p, cam = random_tiny_scene(0, n=5)
     with pytest.raises(ValueError):
         absorb(p, scenes.ramp_palette(), cam, 0.0)
+
+
+# ---------------------------------------------- FP64 depth order and near ties
+def behind_eye_camera(w=65):
+    # eye at z = -1 looking down +z: a particle at world z has z_c = z + 1, and
+    # the axis lands on the centre of pixel (32, 32) of a 65 x 65, fov 90 image
+    return {"eye": (0.0, 0.0, -1.0), "target": (0.0, 0.0, 0.0), "up": (0.0, 1.0, 0.0),
+            "fov_y_deg": 90.0, "width": w, "height": w, "z_near": 1e-3}
+
+
+def sub_ulp_pair():
+    # particle 0 (blue) at world z = 1 + 2^-23, particle 1 (red) at z = 1: the
+    # depths 2 + 2^-23 and 2 differ in FP64 but both round to 2.0f, so an FP32
+    # depth key ties them and would put particle 0 in front by index
+    z_blue = float(np.nextafter(np.float32(1.0), np.float32(2.0)))
+    return parts_of([[0.0, 0.0, z_blue, 0.2, 1.0, 1.0], [0.0, 0.0, 1.0, 0.2, 1.0, 0.0]])
+
+
+def test_depths_closer_than_a_float_ulp_are_crossed_in_true_order():
+    p = sub_ulp_pair()
+    assert np.float32(2.0 + 2.0 ** -23) == np.float32(2.0)   # the keys would tie in FP32
+    cam = behind_eye_camera()
+    g = 1.0 - math.exp(-1.0)
+    # red (index 1) is nearer in FP64: blue is crossed first, then red
+    want = [g, 0.0, g * math.exp(-1.0)]
+    np.testing.assert_allclose(absorb(p, RED_BLUE, cam)[32, 32], want, rtol=1e-12)
+    np.testing.assert_allclose(absorb(p, RED_BLUE, cam, brute=True)[32, 32], want, rtol=1e-12)
+    px = np.array([32], np.int32)
+    got = oracle.render_pixels(p, RED_BLUE, cam, {"mode": 2, "absorption": 1.0}, px, px)
+    np.testing.assert_allclose(got[0], want, rtol=1e-12)
+
+
+def test_near_tie_mass_covers_the_swapped_order():
+    p = sub_ulp_pair()
+    cam = behind_eye_camera()
+    q = {"mode": 2, "absorption": 1.0}
+    B, _ = oracle.ambiguity(p, RED_BLUE, cam, q)
+    # both contributions at the centre: brightness * I * w * (largest palette
+    # value) = 1 each; the other order differs by g (1 - 1/e) per channel
+    np.testing.assert_allclose(B[32, 32], [2.0, 2.0, 2.0], rtol=1e-12)
+    g = 1.0 - math.exp(-1.0)
+    swapped = np.array([g * math.exp(-1.0), 0.0, g])
+    assert np.all(np.abs(swapped - absorb(p, RED_BLUE, cam)[32, 32]) <= B[32, 32])
+    # depths 1e-3 apart are never swapped: no mass at the centre (no clip edge there)
+    far = dict(p)
+    far["z"] = np.array([1.001, 1.0], np.float32)
+    B2, _ = oracle.ambiguity(far, RED_BLUE, cam, q)
+    assert np.all(B2[32, 32] == 0.0)
+    # no mass where only one of the tied pair reaches the pixel: move the blue
+    # particle sideways so that its disc misses the red one's far edge
+    side = dict(p)
+    side["x"] = np.array([-0.3, 0.0], np.float32)      # x_s of blue = 32.5 + 4.875 px
+    Bs, _ = oracle.ambiguity(side, RED_BLUE, cam, q)
+    rec = oracle.project(side, RED_BLUE, cam, q)
+    reach = lambda k, i, j: ((i + 0.5 - rec["xs"][k]) ** 2 + (j + 0.5 - rec["ys"][k]) ** 2
+                             <= rec["r"][k] ** 2)
+    for i in range(65):
+        both = reach(0, i, 32) and reach(1, i, 32)
+        only = reach(0, i, 32) != reach(1, i, 32)
+        if both:
+            assert Bs[32, i, 0] > 0.0
+        if only and not np.any(np.abs(np.hypot(i + 0.5 - rec["xs"], 0.0) - rec["r"]) < 1e-3):
+            assert Bs[32, i, 0] == 0.0
+
+
+def near_tie_scene(seed):
+    # a tiny scene plus copies of some particles moved by one float ulp in z:
+    # exact near ties in depth that share most of their pixels
+    p, cam = random_tiny_scene(seed, n=60)
+    k = np.arange(0, 60, 3)
+    out = {key: np.concatenate([v, v[k]]) for key, v in p.items()}
+    out["z"][60:] = np.nextafter(p["z"][k], np.float32(9.0))
+    out["s"][60:] = 1.0 - p["s"][k]
+    return out, cam
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_selected_pixels_equal_the_full_image_in_every_mode(seed):
+    p, cam = near_tie_scene(seed)
+    pal = scenes.ramp_palette()
+    H, W = cam["height"], cam["width"]
+    py, px = np.mgrid[0:H, 0:W]
+    px, py = px.ravel().astype(np.int32), py.ravel().astype(np.int32)
+    for q in ({}, {"mode": 1}, {"mode": 2, "absorption": 0.7}, {"mode": 2, "absorption": 3.0}):
+        img = oracle.render(p, pal, cam, q)
+        B, _ = oracle.ambiguity(p, pal, cam, q)
+        vals, mass = oracle.render_pixels(p, pal, cam, q, px, py, nthreads=3, with_mass=True)
+        np.testing.assert_allclose(vals, img.reshape(-1, 3), rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(mass, B.reshape(-1, 3), rtol=1e-12, atol=1e-300)
+    # the near ties do put mass on pixels that no clip edge reaches
+    q = {"mode": 2, "absorption": 0.7}
+    assert oracle.ambiguity(p, pal, cam, q)[0].sum() > 10 * oracle.ambiguity(
+        {k: v[:60] for k, v in p.items()}, pal, cam, q)[0].sum()
+
+
+def test_selected_pixels_reject_pixels_off_the_image():
+    p, cam = random_tiny_scene(0, n=5)
+    with pytest.raises(ValueError):
+        oracle.render_pixels(p, scenes.ramp_palette(), cam, {"mode": 2}, np.array([cam["width"]]),
+                             np.array([0]))
