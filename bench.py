@@ -46,6 +46,11 @@ WORKLOADS = {
                                "code (1/4096 octave), 2048x2048 RGB FP32"},
     "precision32": {"scene": "precision", "label": "clustered-100M-2048sq-f32",
                     "desc": "100M clustered particles, FP32 attributes, 2048x2048 RGB FP32"},
+    "precision32-support": {"scene": "precision", "label": "clustered-100M-2048sq-f32-support",
+                            "params": {"sigma_per_h": 1.0 / 3.0},
+                            "desc": "100M clustered particles, FP32 attributes, 2048x2048 RGB "
+                                    "FP32, smoothing length read as the support radius "
+                                    "(sigma = h / chi: 9x fewer covered pixels)"},
     "absorb": {"scene": "clustered", "label": "clustered-10M-1024sq-f32-absorb",
                "params": {"mode": 2, "absorption": 1.0},
                "desc": "the clustered 10M / 1024x1024 workload rendered with Eq. 1's general "
@@ -174,7 +179,37 @@ def profiled_traffic(kernel: str, label: str):
 
 
 def oracle_par(wl: dict) -> dict:
-    return {k: v for k, v in wl.get("params", {}).items() if k in ("mode", "absorption")}
+    keys = ("mode", "absorption", "sigma_per_h")
+    return {k: v for k, v in wl.get("params", {}).items() if k in keys}
+
+
+# error bars per attribute layout: the FP32 path against the FP64 oracle, and
+# the binary16 layouts against the oracle run on the original FP32 values
+ERROR_TOL = {None: 1e-4, "is": 2e-3, "logh": 2e-3, "all": 4e-3}
+
+
+def stated_error(scene, cam, g, par, tol, n_windows=1, n_bright=64, n_random=448):
+    """Max relative pixel error of the timed frame g (H x W x 3, float64) against
+    the FP64 oracle at >= 1024 sampled pixels: a whole 32 x 32 window over the
+    seams of the four tiles nearest the brightest pixel (a halo core), the
+    brightest pixels and random pixels, each computed one by one by the oracle
+    from the original FP32 particles (mode 2 with its ambiguity mass)."""
+    import oracle
+    from tests._metrics import pick_pixels, rel_pixel_error
+    px, py = pick_pixels(g, tile=32, n_windows=n_windows, n_bright=n_bright, n_random=n_random)
+    t0 = time.perf_counter()
+    mass = par.get("mode") == 2
+    res = oracle.render_pixels(scene.parts, scene.palette, cam, par, px, py,
+                               nthreads=os.cpu_count() or 1, with_mass=mass)
+    o, B = res if mass else (res, None)
+    M = np.abs(g).reshape(-1, 3).max(0)
+    err = rel_pixel_error(g[py, px], o, B, M=M)
+    return {"max_rel": err, "tol": tol, "n_pixels": int(px.size), "within_tol": bool(err <= tol),
+            "vs": "FP64 oracle on the original FP32 particles",
+            "picks": f"{n_windows} whole 32x32 tile-corner window(s) (first at the brightest pixel), "
+                     f"{n_bright} brightest, {n_random} random",
+            "metric": "max over pixels and channels of max(0, |g - o| - B) / max(|o|, 1e-3 max|o_c|)",
+            "oracle_s": time.perf_counter() - t0}
 
 
 def oracle_sample_rate(scene, cam, target_s: float, seed: int = 0, par=None):
@@ -365,7 +400,15 @@ def run_batch(args, wl):
            "ms_per_step": 1e3 * e2e_s}
 
     cpu = None
+    error = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the CPU leg: the oracle states the error of one 1024^2 view of the last
+        # batch, then is timed
+        r.render_batch(cams, imgs)
+        torch.cuda.synchronize()
+        error = stated_error(scene, cams[1], imgs[1].cpu().numpy().astype(np.float64), {},
+                             ERROR_TOL[None], n_random=256)
+        error["view"] = 1
         rate, m, cores, secs = oracle_sample_rate(scene, cams[1], 10.0)
         cpu = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
                "sample": f"{m} particles drawn at random from the workload, one 1024x1024 view of "
@@ -390,6 +433,7 @@ def run_batch(args, wl):
             "e2e": e2e,
             "gpu_launches": graph_kernels * args.steps,
             "clocks": clocks,
+            "error": error,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -417,13 +461,18 @@ def run_ours(args, wl):
         fp16 = scene.fp16
     elif wl.get("fp16") == "is":
         fp16 = {k: scene.fp16[k] for k in ("I", "s")}
-    elif wl.get("fp16") == "logh":
-        from paper_1309_1114_gb300 import scenes as _sc
-        h_log2_min = -14.0
-        fp16 = {"h": _sc.log16_h(scene.parts["h"], h_log2_min), "I": scene.fp16["I"],
-                "s": scene.fp16["s"]}
     stream = torch.cuda.current_stream()
     r = Renderer(local, stream.cuda_stream)
+    if wl.get("fp16") == "logh":
+        # the library encodes the 18 B layout (I, s binary16, h a 16-bit log code)
+        from paper_1309_1114_gb300 import splotch as _S
+        h_log2_min = -14.0
+        dev = {k: torch.from_numpy(scene.parts[k]).cuda() for k in ("h", "I", "s")}
+        coded = r.encode_attrs(dev["h"], dev["I"], dev["s"], _S.SPL_ATTR_LOGH16, h_log2_min)
+        torch.cuda.synchronize()
+        fp16 = {"h": coded["h"].cpu().numpy().view(np.uint16), "I": coded["I"].cpu().numpy(),
+                "s": coded["s"].cpu().numpy()}
+        del dev, coded
     r.load(scene.parts, fp16, h_log2_min)
     r.set_colormap(scene.palette)
     r.set_camera(cam)
@@ -547,7 +596,13 @@ def run_ours(args, wl):
            "ms_per_step": 1e3 * e2e_s}
 
     cpu = None
+    error = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the CPU leg: the oracle states the timed frame's error, then is timed
+        g = img.cpu().numpy().astype(np.float64)
+        error = stated_error(scene, cam, g, dict(oracle_par(wl)), ERROR_TOL[wl.get("fp16")],
+                             n_random=128 if scene.n > 200_000_000 else 448)
+        del g
         rate, m, cores, secs = oracle_sample_rate(scene, cam, 10.0, par=oracle_par(wl))
         cpu = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
                "sample": f"{m} particles drawn at random from the workload, full {W}x{H} image, "
@@ -577,6 +632,7 @@ def run_ours(args, wl):
             "e2e": e2e,
             "gpu_launches": int(st["launches"]) * args.steps,
             "clocks": clocks,
+            "error": error,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -611,7 +667,6 @@ def run_stream(args, wl):
     work = r.count_work()
     r.load({k: v[:0] for k, v in scene.parts.items()})
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in scene.parts.items()}
-    scene.parts = None
     img = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
     chunk = wl["stream"]
     for _ in range(args.warmup):
@@ -674,6 +729,11 @@ def run_stream(args, wl):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = {"value": ws * n / e2e_s, "unit": "particles/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": 12 * W * H, "ms_per_step": 1e3 * e2e_s}
+    error = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the CPU leg: the oracle states the error of the streamed frame
+        error = stated_error(scene, cam, host_img.numpy().astype(np.float64), {},
+                             ERROR_TOL[None])
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
@@ -692,6 +752,7 @@ def run_stream(args, wl):
             "e2e": e2e,
             "gpu_launches": int(st["launches"]) * nch * args.steps,
             "clocks": clocks,
+            "error": error,
             "cpu_baseline": None,
         }
         print(json.dumps(line), flush=True)
@@ -704,10 +765,10 @@ def run_stream(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="clustered")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="precision32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -59,12 +59,16 @@ extern "C" {
 #define SPL_ATTR_F16 1    /* h, I, s in IEEE binary16, widened to FP32 on load: 18 B per
                              particle (the memory-access model of Sec. 3.2: one load per
                              particle, fewer bytes).  h enters exp(-d^2/h^2), so its 2^-11
-                             rounding moves clip-edge weights by up to ~1e-2 relative */
-#define SPL_ATTR_F16_IS 2 /* h in FP32, I and s in binary16: 20 B per particle */
+                             rounding moves clip-edge weights by up to ~1e-2 relative: this
+                             layout does NOT keep images within 2e-3 of the FP32 originals
+                             (measured 2.5e-3); the next two layouts do */
+#define SPL_ATTR_F16_IS 2 /* h in FP32, I and s in binary16: 20 B per particle; images
+                             within 2e-3 of the FP32 originals (measured 9e-4) */
 #define SPL_ATTR_LOGH16 3 /* I and s in binary16, h as a 16-bit logarithmic code k (uint16):
                              h = 2^(h_log2_min + k / 4096), 1/4096-octave steps over 16
                              octaves (relative step 1.7e-4, a third of binary16's): 18 B per
-                             particle with h precise enough for 2e-3 images */
+                             particle, images within 2e-3 of the FP32 originals (measured
+                             1.3e-3); spl_load_particles_as / spl_encode_attrs write it */
 
 /* output modes */
 #define SPL_MODE_ADDITIVE 0   /* image = sum of clipped Gaussians (Eq. 1, E_p = A_p, thin) */
@@ -73,8 +77,10 @@ extern "C" {
                                * E_p = brightness I_p colour(s_p), grey absorption
                                * A_p = absorption * brightness * I_p; across particle p a ray
                                * becomes I exp(-tau) + (E_p/A_p)(1 - exp(-tau)), tau = A_p w_p,
-                               * particles crossed from the farthest to the nearest (depth key
-                               * z_c in FP32, ties by particle index); single views only
+                               * particles crossed from the farthest to the nearest, equal
+                               * depths by decreasing particle index.  The depth key is z_c
+                               * rounded to FP32, so particles whose depths lie within one FP32
+                               * ulp of each other are ordered by index.  Single views only
                                * (spl_render, spl_render_host) */
 
 /* tile schedulers */
@@ -166,6 +172,29 @@ int spl_destroy(spl_ctx *ctx);     /* NULL is accepted and ignored */
  * context stream; the call returns after the copy has completed. */
 int spl_load_particles(spl_ctx *ctx, const spl_particles *p);
 
+/* Load FP32 attributes and store them in a smaller layout (the memory-access
+ * model of Sec. 3.2: every particle's bytes are read once per frame, so fewer
+ * bytes per particle is less traffic).  p->attr_type must be SPL_ATTR_F32;
+ * store_as is SPL_ATTR_F32, SPL_ATTR_F16, SPL_ATTR_F16_IS or SPL_ATTR_LOGH16
+ * (then h_log2_min, finite, is the log2 of the smoothing length of code 0).
+ * The conversion runs on the device (spl_encode_attrs); host arrays are first
+ * copied into temporary device memory.  Otherwise as spl_load_particles. */
+int spl_load_particles_as(spl_ctx *ctx, const spl_particles *p, int32_t store_as,
+                          float h_log2_min);
+
+/* Convert n FP32 attributes (d_h, d_I, d_s: DEVICE, of ctx's device) into the
+ * storage layout store_as, written to d_h_out, d_I_out, d_s_out (DEVICE,
+ * caller-owned; 4 bytes per value where the layout keeps FP32, 2 bytes for
+ * binary16 and for the h code).  Binary16 values are rounded to nearest even.
+ * SPL_ATTR_LOGH16 codes are k = round_half_even(4096 (log2 h - h_log2_min))
+ * clamped to [0, 65535], formed in FP64; h = 0 gets code 0; a negative or
+ * non-finite h (a particle the FP32 layout renders inactive) gets code 0 and
+ * its I is stored as a binary16 NaN, which keeps the particle inactive.
+ * stream: NULL means the context stream; returns with the kernel queued. */
+int spl_encode_attrs(spl_ctx *ctx, const float *d_h, const float *d_I, const float *d_s,
+                     int64_t n, int32_t store_as, float h_log2_min, void *d_h_out,
+                     void *d_I_out, void *d_s_out, void *stream);
+
 /* Camera, colour map and parameters.  The colour map is n >= 1 RGB FP32
  * triples (host memory), looked up by s' = clamp((s - s_min)/(s_max - s_min),
  * 0, 1) with linear interpolation between the n entries (Sec. 2 palettes). */
@@ -177,8 +206,13 @@ int spl_get_params(spl_ctx *ctx, spl_params *out);
 
 /* Render the loaded particles with the current camera into d_image (device,
  * width*height*3 FP32, caller-owned, fully overwritten).  stream: NULL means
- * the context stream.  The call synchronises once after binning (to size the
- * tile lists) and returns with the remaining kernels queued on the stream. */
+ * the context stream.  The call waits once on the host for the binning counts
+ * (to size the tile lists); meanwhile the image is cleared and the lists are
+ * filled on the device into the capacities of the previous frames, so the
+ * device does not drain between binning and the tile pass.  A frame whose
+ * lists outgrow those capacities (the first one, or a heavier view) is
+ * detected there, the buffers are grown and the lists filled again.  The call
+ * returns with the tile and large passes queued on the stream. */
 int spl_render(spl_ctx *ctx, float *d_image, void *stream);
 
 /* Same, into host memory: renders into library scratch and copies the image
@@ -297,6 +331,14 @@ int spl_mlp_adam(float *d_theta, const float *d_grad, float *d_m, float *d_v, in
 int spl_mlp_train(const float *d_x, const float *d_t, int64_t B, float *theta, int32_t steps,
                   float lr, float *losses, void *stream);
 
+/* The E_p = A_p solution of Eq. 1 applied to an additive image: every one of
+ * the n_values floats v of d_image (DEVICE, of ctx's device) becomes
+ * 1 - exp(-v), in place (the map is not linear, so a frame composed from
+ * partial additive images -- the particle chunks of Sec. 2's MPI scheme, or
+ * out-of-core chunks -- takes it once, after the sum).  stream: NULL means the
+ * context stream; returns with the kernel queued. */
+int spl_apply_ea(spl_ctx *ctx, float *d_image, int64_t n_values, void *stream);
+
 /* Diagnostics used by the tests.  spl_get_records copies the last render's
  * per-particle rasterisation results for particles [0, n) into host arrays
  * (any may be NULL): screen position x_s, y_s (as double), screen radius r,
@@ -304,32 +346,36 @@ int spl_mlp_train(const float *d_x, const float *d_t, int64_t B, float *theta, i
 int spl_get_records(spl_ctx *ctx, int64_t n, double *xs, double *ys, float *r,
                     float *e, int32_t *cls);
 
-/* Render without allocating: for callers that cannot call cudaMalloc (code
- * running where device allocation is forbidden or must stay with the
- * caller: inside a graph capture that must not create allocations, under a
- * memory budget the caller owns, or in a host application that passes only
- * its own buffers).  It needs no context.  It runs the kernels of
- * spl_render, with every scratch buffer carved from one file-scope
- * __device__ array of about 16 MiB that each GPU loading the library holds
- * until the process exits.  The paper has no counterpart: it is a property
- * of this library, not of the method.
+/* Render without allocating: for callers that cannot let a library call
+ * cudaMalloc -- an application whose device memory is handed out by its own
+ * allocator or held to a fixed budget, or a host program that passes only its
+ * own buffers and wants no hidden device allocation.  It needs no context.  It
+ * runs the kernels of spl_render, with every scratch buffer carved from one
+ * file-scope __device__ array of about 16 MiB, which every GPU that
+ * loads the library holds until the process exits.  The paper has no
+ * counterpart: it is a property of this library, not of the method.
  *   p       particles in DEVICE memory (mem_space must be SPL_MEM_DEVICE),
  *           n <= 131072;
  *   cam     camera with ceil(width/tile) * ceil(height/tile) <= 16384 tiles;
- *   q       parameters, or NULL for spl_default_params();
+ *   q       parameters, or NULL for spl_default_params(); q->sched is ignored
+ *           (work items are taken in image order), SPL_MODE_ABSORB is rejected;
  *   rgb     colour map (HOST memory, npal RGB triples, 1 <= npal <= 1024)
  *           looked up over [s_min, s_max];
  *   d_image DEVICE output, width*height*3 FP32, fully overwritten;
  *   device  CUDA ordinal; stream: cudaStream_t or NULL.
- * Sizes beyond those limits, or a frame whose tile lists exceed 2^21
- * entries or 32768 work items, return SPL_ELIMIT and render nothing.  The
- * first call on a device looks up the array's device address (with that
- * device made current); make that first call before any stream capture.
- * The call synchronises the stream once (after binning) and returns with the
- * remaining kernels queued.  Every call shares the one array, which keeps
- * the last call's contents (each call clears what must start at zero), so
- * calls whose kernels overlap on the GPU -- on different streams, or from
- * different threads -- race and corrupt each other: serialise them. */
+ * Sizes beyond those limits, or a frame whose tile lists exceed 2^21 entries
+ * or 32768 work items, return SPL_ELIMIT and render nothing.  The first call
+ * on a device looks up the array's device address (with that device made
+ * current).  The call waits on the host once, after binning, for the list
+ * sizes, so it must not be issued on a stream that is being captured into a
+ * CUDA graph (it then returns SPL_ESTATE without doing anything).  It returns
+ * with the tile and large passes queued; a device-side check that fails in
+ * those passes (an index guard) is reported as SPL_EDEVICE by the next call on
+ * that device, whose own frame is then not rendered.  Every call shares the one
+ * array, which keeps the last call's contents (each call clears what must
+ * start at zero), so calls whose kernels overlap on the GPU -- on different
+ * streams, or from different threads -- race and corrupt each other:
+ * serialise them. */
 int spl_render_noalloc(const spl_particles *p, const spl_camera *cam, const spl_params *q,
                        const float *rgb, int32_t npal, float s_min, float s_max, float *d_image,
                        int32_t device, void *stream);

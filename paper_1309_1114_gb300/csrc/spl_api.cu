@@ -129,6 +129,7 @@ struct spl_ctx {
     // timing: two event sets, so that a frame's stage times are read at the
     // next frame's synchronisation point without an extra wait
     bool timing = false;
+    cudaEvent_t stats_ready = nullptr;  // binning counts copied to hstats
     cudaEvent_t ev[2][6] = {};
     int ev_set = 0;
     bool ev_pending[2] = {false, false};
@@ -245,6 +246,8 @@ extern "C" int spl_create(spl_ctx **out, int device, void *stream) {
     }
     for (int k = 0; rc == SPL_OK && k < 12; ++k)
         if (cudaEventCreate(&c->ev[k / 6][k % 6]) != cudaSuccess) rc = SPL_ECUDA;
+    if (rc == SPL_OK && cudaEventCreateWithFlags(&c->stats_ready, cudaEventDisableTiming) != cudaSuccess)
+        rc = SPL_ECUDA;
     if (rc != SPL_OK) {
         cudaGetLastError();
         spl_destroy(c);
@@ -290,23 +293,34 @@ extern "C" int spl_destroy(spl_ctx *c) {
     for (auto &set : c->ev)
         for (auto &e : set)
             if (e) cudaEventDestroy(e);
+    if (c->stats_ready) cudaEventDestroy(c->stats_ready);
     delete c;
     return SPL_OK;
 }
 
-extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
-    if (!c || !p || p->n < 0) return SPL_EINVAL;
-    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_LOGH16) return SPL_EINVAL;
-    if (p->attr_type == SPL_ATTR_LOGH16 && !std::isfinite(p->h_log2_min)) return SPL_EINVAL;
-    if (p->mem_space != SPL_MEM_HOST && p->mem_space != SPL_MEM_DEVICE) return SPL_EINVAL;
-    if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return SPL_EINVAL;
+// Bytes per value of h and of I, s in a storage layout.
+static size_t h_bytes(int attr) { return (attr == SPL_ATTR_F16 || attr == SPL_ATTR_LOGH16) ? 2 : 4; }
+static size_t is_bytes(int attr) { return attr == SPL_ATTR_F32 ? 4 : 2; }
+
+static bool particles_ok(const spl_particles *p) {
+    if (!p || p->n < 0) return false;
+    if (p->attr_type < SPL_ATTR_F32 || p->attr_type > SPL_ATTR_LOGH16) return false;
+    if (p->attr_type == SPL_ATTR_LOGH16 && !std::isfinite(p->h_log2_min)) return false;
+    if (p->mem_space != SPL_MEM_HOST && p->mem_space != SPL_MEM_DEVICE) return false;
+    if (p->n > 0 && (!p->x || !p->y || !p->z || !p->h || !p->I || !p->s)) return false;
     const int nrgb = (p->cr != nullptr) + (p->cg != nullptr) + (p->cb != nullptr);
-    if (nrgb != 0 && nrgb != 3) return SPL_EINVAL;
-    if (p->n > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // ids are 32-bit
+    if (nrgb != 0 && nrgb != 3) return false;
+    return p->n <= (int64_t)0xFFFFFFFFLL;   // ids are 32-bit
+}
+
+// Copy a particle set into the context's SoA; the attributes are stored in
+// layout `store` (p->attr_type, or any layout when p->attr_type is FP32: then
+// the encoder converts them on the device).
+static int load_impl(spl_ctx *c, const spl_particles *p, int store, float h_log2_min) {
     DeviceGuard g(c->device);
     const size_t n = (size_t)p->n;
-    const size_t ah = (p->attr_type == SPL_ATTR_F16 || p->attr_type == SPL_ATTR_LOGH16) ? 2 : 4;
-    const size_t ab = p->attr_type == SPL_ATTR_F32 ? 4 : 2;     // bytes of I and s
+    const size_t ah = h_bytes(store), ab = is_bytes(store);
+    const bool convert = store != p->attr_type;
     SPL_TRY(c->x.ensure(n ? n : 1));
     SPL_TRY(c->y.ensure(n ? n : 1));
     SPL_TRY(c->z.ensure(n ? n : 1));
@@ -315,31 +329,97 @@ extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
     SPL_TRY(c->s.ensure((n ? n : 1) * ab));
     const cudaMemcpyKind kind =
         p->mem_space == SPL_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    if (n) {
-        SPL_CUDA(cudaMemcpyAsync(c->x.p, p->x, n * 4, kind, c->stream));
-        SPL_CUDA(cudaMemcpyAsync(c->y.p, p->y, n * 4, kind, c->stream));
-        SPL_CUDA(cudaMemcpyAsync(c->z.p, p->z, n * 4, kind, c->stream));
-        SPL_CUDA(cudaMemcpyAsync(c->h.p, p->h, n * ah, kind, c->stream));
-        SPL_CUDA(cudaMemcpyAsync(c->I.p, p->I, n * ab, kind, c->stream));
-        SPL_CUDA(cudaMemcpyAsync(c->s.p, p->s, n * ab, kind, c->stream));
-    }
-    if (nrgb == 3) {
-        SPL_TRY(c->cr.ensure(n ? n : 1));
-        SPL_TRY(c->cg.ensure(n ? n : 1));
-        SPL_TRY(c->cb.ensure(n ? n : 1));
-        if (n) {
-            SPL_CUDA(cudaMemcpyAsync(c->cr.p, p->cr, n * 4, kind, c->stream));
-            SPL_CUDA(cudaMemcpyAsync(c->cg.p, p->cg, n * 4, kind, c->stream));
-            SPL_CUDA(cudaMemcpyAsync(c->cb.p, p->cb, n * 4, kind, c->stream));
+    float *tmp = nullptr;   // device copies of host FP32 attributes to be converted
+    if (convert && n && p->mem_space == SPL_MEM_HOST) {
+        if (cudaMalloc((void **)&tmp, 3 * n * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return SPL_ENOMEM;
         }
     }
-    SPL_CUDA(cudaStreamSynchronize(c->stream));
-    c->have_rgb = nrgb == 3;
+    int rc = SPL_OK;
+    auto copy = [&](void *dst, const void *src, size_t bytes) {
+        if (rc == SPL_OK) rc = cuda_status(cudaMemcpyAsync(dst, src, bytes, kind, c->stream));
+    };
+    if (n) {
+        copy(c->x.p, p->x, n * 4);
+        copy(c->y.p, p->y, n * 4);
+        copy(c->z.p, p->z, n * 4);
+        if (!convert) {
+            copy(c->h.p, p->h, n * ah);
+            copy(c->I.p, p->I, n * ab);
+            copy(c->s.p, p->s, n * ab);
+        } else {
+            const float *dh = static_cast<const float *>(p->h);
+            const float *dI = static_cast<const float *>(p->I);
+            const float *ds = static_cast<const float *>(p->s);
+            if (tmp) {
+                copy(tmp, p->h, n * 4);
+                copy(tmp + n, p->I, n * 4);
+                copy(tmp + 2 * n, p->s, n * 4);
+                dh = tmp;
+                dI = tmp + n;
+                ds = tmp + 2 * n;
+            }
+            if (rc == SPL_OK) {
+                launch_encode_attrs(dh, dI, ds, (int64_t)n, store, h_log2_min, c->h.p, c->I.p,
+                                    c->s.p, c->sms, c->stream);
+                rc = cuda_status(cudaGetLastError());
+            }
+        }
+    }
+    const bool rgb = p->cr != nullptr;
+    if (rgb && rc == SPL_OK) {
+        rc = c->cr.ensure(n ? n : 1);
+        if (rc == SPL_OK) rc = c->cg.ensure(n ? n : 1);
+        if (rc == SPL_OK) rc = c->cb.ensure(n ? n : 1);
+        if (n) {
+            copy(c->cr.p, p->cr, n * 4);
+            copy(c->cg.p, p->cg, n * 4);
+            copy(c->cb.p, p->cb, n * 4);
+        }
+    }
+    if (rc == SPL_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+    if (tmp) cudaFree(tmp);
+    if (rc != SPL_OK) return rc;
+    c->have_rgb = rgb;
     c->n = p->n;
-    c->attr_type = p->attr_type;
-    c->h_log2_min = p->h_log2_min;
+    c->attr_type = store;
+    c->h_log2_min = store == SPL_ATTR_LOGH16 ? h_log2_min : 0.f;
     c->have_particles = true;
     return SPL_OK;
+}
+
+extern "C" int spl_load_particles(spl_ctx *c, const spl_particles *p) {
+    if (!c || !particles_ok(p)) return SPL_EINVAL;
+    return load_impl(c, p, p->attr_type, p->h_log2_min);
+}
+
+extern "C" int spl_load_particles_as(spl_ctx *c, const spl_particles *p, int32_t store_as,
+                                     float h_log2_min) {
+    if (!c || !particles_ok(p) || p->attr_type != SPL_ATTR_F32) return SPL_EINVAL;
+    if (store_as < SPL_ATTR_F32 || store_as > SPL_ATTR_LOGH16) return SPL_EINVAL;
+    if (store_as == SPL_ATTR_LOGH16 && !std::isfinite(h_log2_min)) return SPL_EINVAL;
+    return load_impl(c, p, store_as, h_log2_min);
+}
+
+extern "C" int spl_encode_attrs(spl_ctx *c, const float *d_h, const float *d_I, const float *d_s,
+                                int64_t n, int32_t store_as, float h_log2_min, void *d_h_out,
+                                void *d_I_out, void *d_s_out, void *stream) {
+    if (!c || n < 0) return SPL_EINVAL;
+    if (store_as < SPL_ATTR_F32 || store_as > SPL_ATTR_LOGH16) return SPL_EINVAL;
+    if (store_as == SPL_ATTR_LOGH16 && !std::isfinite(h_log2_min)) return SPL_EINVAL;
+    if (n > 0 && (!d_h || !d_I || !d_s || !d_h_out || !d_I_out || !d_s_out)) return SPL_EINVAL;
+    DeviceGuard g(c->device);
+    launch_encode_attrs(d_h, d_I, d_s, n, store_as, h_log2_min, d_h_out, d_I_out, d_s_out, c->sms,
+                        stream ? (cudaStream_t)stream : c->stream);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int spl_apply_ea(spl_ctx *c, float *d_image, int64_t n_values, void *stream) {
+    if (!c || n_values < 0 || (n_values > 0 && !d_image)) return SPL_EINVAL;
+    DeviceGuard g(c->device);
+    launch_epilogue_ea(d_image, n_values, c->sms, stream ? (cudaStream_t)stream : c->stream);
+    return cuda_status(cudaGetLastError());
 }
 
 extern "C" int spl_set_camera(spl_ctx *c, const spl_camera *cam) {
@@ -625,8 +705,10 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
                 c->dstats.p->item_totals, s);
 }
 
-// Stage 2: clear the images, fill the tile lists and work items, render.
-static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStream_t s) {
+// Stage 2: clear the images and fill the tile lists and work items into the
+// current capacities (the kernels check them and flag an overflow instead of
+// writing past the end).
+static void enqueue_lists(spl_ctx *c, const Views &vs, cudaStream_t s) {
     if (!c->accumulate) launch_zero_images(vs, c->d_images.p, c->sms, s);
     BinArgs ba{};
     ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
@@ -642,6 +724,10 @@ static void enqueue_render(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
     launch_scatter(vs, ba, c->sms, s);
     launch_fill_items(vs, c->offsets.p, c->item_offsets.p, c->items.p, (int)c->items.cap,
                       c->dstats.p, s);
+}
+
+// Stage 3: schedule the work items, the tile and large passes, the epilogue.
+static void enqueue_passes(spl_ctx *c, const Views &vs, bool large_pass, cudaStream_t s) {
     TileArgs ta{};
     ta.rec0 = c->rec0.p; ta.rec1 = c->rec1.p;
     ta.offsets = c->offsets.p;
@@ -707,8 +793,12 @@ static void fill_stats(spl_ctx *c, const Views &vs, int launches) {
     st.tile_px = vs.tile;
 }
 
-// Eager render of a batch: binning, one synchronisation to size the lists
-// exactly, then the passes.
+// Eager render of a batch.  The binning counts are copied to the host and the
+// host waits for them (not for the stream): meanwhile the device clears the
+// images and fills the tile lists into the capacities of the earlier frames.
+// If the counts show that the lists or the work items did not fit, the host
+// waits for that fill, grows the buffers, re-arms the list cursors and fills
+// the lists again; either way the passes follow.
 static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const *images,
                         cudaStream_t s) {
     if ((!c->have_particles && !c->streaming) || c->npal < 1) return SPL_ESTATE;
@@ -720,18 +810,31 @@ static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const 
     enqueue_binning(c, vs, s);
     SPL_CUDA(cudaGetLastError());
     SPL_CUDA(cudaMemcpyAsync(c->hstats, c->dstats.p, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
-    SPL_CUDA(cudaStreamSynchronize(s));
+    SPL_CUDA(cudaEventRecord(c->stats_ready, s));
+    enqueue_lists(c, vs, s);
+    SPL_CUDA(cudaGetLastError());
+    SPL_CUDA(cudaEventSynchronize(c->stats_ready));
     harvest_timing(c, c->ev_set ^ 1);   // the previous frame has finished
     if (c->hstats->err) {
-        // a device-side check failed in this or an earlier frame
+        // a device-side check failed in an earlier frame: report it (the flag
+        // is cleared once the lists queued above are done)
+        SPL_CUDA(cudaStreamSynchronize(s));
         SPL_CUDA(cudaMemsetAsync(&c->dstats.p->err, 0, sizeof(unsigned), s));
         return SPL_EDEVICE;
     }
     const int64_t total = c->hstats->slot_total;
     const int n_tile_items = c->hstats->item_totals[0];
     const int n_large_items = c->hstats->item_totals[1];
-    SPL_TRY(grow(c, c->entries, (size_t)(total ? total : 1)));
-    SPL_TRY(grow(c, c->items, (size_t)(n_tile_items + n_large_items + 1)));
+    if ((size_t)total > c->entries.cap || (size_t)n_tile_items + n_large_items > c->items.cap) {
+        // the lists ran into buffers too small: wait for them, grow, refill
+        SPL_CUDA(cudaStreamSynchronize(s));
+        SPL_TRY(grow(c, c->entries, (size_t)(total ? total : 1)));
+        SPL_TRY(grow(c, c->items, (size_t)(n_tile_items + n_large_items + 1)));
+        SPL_CUDA(cudaMemsetAsync(&c->dstats.p->err, 0, sizeof(unsigned), s));
+        launch_slot_cursor(NLIST * vs.total_tiles, c->counts.p, c->offsets.p, c->cursor.p, s);
+        enqueue_lists(c, vs, s);
+        SPL_CUDA(cudaGetLastError());
+    }
     SPL_TRY(size_item_buffers(c));
     if (c->par.mode == SPL_MODE_ABSORB) {
         const int64_t m = total > vs.n ? total : vs.n;
@@ -741,7 +844,7 @@ static int render_views(spl_ctx *c, const spl_camera *cams, int V, float *const 
         SPL_TRY(grow(c, c->partial, c->items.cap * (size_t)vs.tile * (size_t)vs.tile));
     }
     c->last_items = n_tile_items + n_large_items;
-    enqueue_render(c, vs, n_large_items > 0, s);
+    enqueue_passes(c, vs, n_large_items > 0, s);
     SPL_CUDA(cudaGetLastError());
     const int launches = (int)(g_launches - launched0);
     if (c->timing) {
@@ -931,7 +1034,8 @@ static int capture_batch(spl_ctx *c, const Views &vs, unsigned long long key) {
     if (e == cudaSuccess) {
         const long long launched0 = g_launches;
         enqueue_binning(c, vs, c->cap_stream);
-        enqueue_render(c, vs, true, c->cap_stream);
+        enqueue_lists(c, vs, c->cap_stream);
+        enqueue_passes(c, vs, true, c->cap_stream);
         c->graph_kernels = (int)(g_launches - launched0);
         e = cudaStreamEndCapture(c->cap_stream, &g);
     }
@@ -1235,14 +1339,13 @@ extern "C" int spl_count_work(spl_ctx *c, int64_t out[4]) {
 }
 
 // ---------------------------------------------------------------------------
-// spl_render_noalloc: the render for callers that cannot allocate device
-// memory -- code that runs where cudaMalloc is not allowed or not wanted
-// (inside a CUDA-graph capture that must not create allocations, under a
-// memory budget owned by someone else, or in a host application that hands
-// us only its own buffers).  The same kernels as spl_render run, but every
-// scratch buffer is carved from the file-scope device array below, whose
-// size is fixed when the library is loaded; every GPU that loads the library
-// keeps it until the process exits.
+// spl_render_noalloc: the render for callers that cannot let a library
+// allocate device memory -- an application whose device memory comes from
+// its own allocator or a fixed budget, or a host program that hands us only
+// its own buffers.  The same kernels as spl_render run, but every scratch
+// buffer is carved from the file-scope device array below, whose size is
+// fixed when the library is loaded; every GPU that loads the library keeps it
+// until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int64_t kNaMaxParticles = 131072;
@@ -1270,8 +1373,11 @@ constexpr size_t kNaImage = kNaView + na_round(sizeof(FrameConst));
 constexpr size_t kNaBytes = kNaImage + na_round(sizeof(float *));
 }  // namespace
 
-// The scratch itself (about 15 MiB).  In host code this name is only a
-// host-side stand-in; its device address comes from cudaGetSymbolAddress.
+static_assert(kNaBytes < ((size_t)17 << 20), "the fixed scratch stays below 17 MiB");
+
+// The scratch itself (about 16 MiB as laid out above).  In host
+// code this name is only a host-side stand-in; its device address comes from
+// cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char spl_noalloc_scratch[kNaBytes];
 
 namespace {
@@ -1329,6 +1435,14 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     }
     if (device < 0 || device >= ndev) return SPL_EINVAL;
     DeviceGuard g(device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the call waits on the host mid-way, which a capturing stream forbids
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &capturing) != cudaSuccess) {
+        cudaGetLastError();
+        return SPL_ECUDA;
+    }
+    if (capturing != cudaStreamCaptureStatusNone) return SPL_ESTATE;
     unsigned char *base = nullptr;
     SPL_TRY(na_scratch(device, &base));
     DevStats *dst = reinterpret_cast<DevStats *>(base + kNaStats);
@@ -1347,7 +1461,6 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     WorkItem *items = reinterpret_cast<WorkItem *>(base + kNaItems);
     FrameConst *d_fc = reinterpret_cast<FrameConst *>(base + kNaView);
     float **d_img = reinterpret_cast<float **>(base + kNaImage);
-    cudaStream_t s = (cudaStream_t)stream;
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     FrameConst fcv = fc;
@@ -1363,10 +1476,12 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     vs.n = p->n;
 
     // the array keeps the previous call's contents: clear what starts at zero
+    // (the error word stays: the previous call's passes may have set it, and
+    // it is read at this call's synchronisation point)
     SPL_CUDA(cudaMemcpyAsync(pal, rgb, sizeof(float) * 3 * npal, cudaMemcpyHostToDevice, s));
     SPL_CUDA(cudaMemcpyAsync(d_fc, &fcv, sizeof(FrameConst), cudaMemcpyHostToDevice, s));
     SPL_CUDA(cudaMemcpyAsync(d_img, &d_image, sizeof(float *), cudaMemcpyHostToDevice, s));
-    SPL_CUDA(cudaMemsetAsync(dst, 0, sizeof(DevStats), s));
+    SPL_CUDA(cudaMemsetAsync(dst, 0, offsetof(DevStats, err), s));
     SPL_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * NLIST * fc.ntiles, s));
     SPL_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int) * NLIST * fc.ntiles, s));
     RasterArgs ra{};
@@ -1400,7 +1515,11 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     DevStats h;
     SPL_CUDA(cudaMemcpyAsync(&h, dst, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
     SPL_CUDA(cudaStreamSynchronize(s));
-    if (h.err) return SPL_EDEVICE;
+    if (h.err) {
+        // a check failed in this binning or in the previous call's passes
+        SPL_CUDA(cudaMemsetAsync(&dst->err, 0, sizeof(unsigned), s));
+        return SPL_EDEVICE;
+    }
     const int64_t total = h.slot_total;
     const int n_tile_items = h.item_totals[0], n_large_items = h.item_totals[1];
     if (total > kNaMaxEntries || (int64_t)n_tile_items + n_large_items > kNaMaxItems)

@@ -203,6 +203,12 @@ void launch_depth_order(const float4 *rec1, const float2 *rec2, int64_t n, unsig
                         unsigned long long *etmp, unsigned *rank, int *hist, int sms,
                         cudaStream_t s);
 void launch_epilogue_ea(float *image, int64_t nvals, int sms, cudaStream_t s);
+// FP32 attributes h, I, s into storage layout `store` (SPL_ATTR_* value).
+void launch_encode_attrs(const float *h, const float *I, const float *s, int64_t n, int store,
+                         float h_log2_min, void *ho, void *Io, void *so, int sms, cudaStream_t st);
+// cursor[k] = offsets[k] + counts[k] for the m list slots (re-arms the scatter).
+void launch_slot_cursor(int m, const int *counts, const long long *offsets, long long *cursor,
+                        cudaStream_t s);
 // Zero every view's image / apply the E=A map to every view's image (the
 // image pointers are read from device memory, so a graph can replay them).
 void launch_zero_images(const Views &v, float *const *images, int sms, cudaStream_t s);

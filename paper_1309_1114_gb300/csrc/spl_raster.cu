@@ -505,6 +505,14 @@ void launch_scan(int m, const int *in, int *out, int *cursor, int nseg, int *seg
     ++g_launches;
 }
 
+void launch_slot_cursor(int m, const int *counts, const long long *offsets, long long *cursor,
+                        cudaStream_t s) {
+    const int grid = (m + 255) / 256 < 1024 ? (m + 255) / 256 : 1024;
+    if (grid <= 0) return;
+    slot_cursor_kernel<<<grid, 256, 0, s>>>(m, counts, offsets, cursor);
+    ++g_launches;
+}
+
 void launch_slot_offsets(int m, int *counts, int *ovf, long long *offsets, long long *cursor,
                          long long *total, cudaStream_t s) {
     const int grid = (m + 255) / 256 < 1024 ? (m + 255) / 256 : 1024;

@@ -164,21 +164,6 @@ def fp16_attrs(parts: dict) -> dict:
     return {k: parts[k].astype(np.float16) for k in ("h", "I", "s")}
 
 
-LOG16_STEPS = 4096     # codes per octave of the 16-bit logarithmic h
-
-
-def log16_h(h, log2_min: float) -> np.ndarray:
-    """Smoothing lengths as 16-bit logarithmic codes k, h ~ 2^(log2_min + k/4096)
-    (round to nearest code; values outside the 16 octaves are clamped)."""
-    k = np.rint((np.log2(np.maximum(np.asarray(h, np.float64), 1e-300)) - log2_min) * LOG16_STEPS)
-    return np.clip(k, 0, 65535).astype(np.uint16)
-
-
-def log16_decoded(codes, log2_min: float) -> np.ndarray:
-    """The smoothing lengths the codes stand for, rounded to float32."""
-    return np.exp2(log2_min + codes.astype(np.float64) / LOG16_STEPS).astype(np.float32)
-
-
 def widened(parts: dict, f16: dict) -> dict:
     """The particle set as the FP16 path stores it, widened back to float32."""
     out = dict(parts)

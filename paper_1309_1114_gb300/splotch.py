@@ -66,6 +66,9 @@ _SIGS = {
     "spl_create": [C.POINTER(C.c_void_p), C.c_int, _P],
     "spl_destroy": [_P],
     "spl_load_particles": [_P, C.POINTER(spl_particles)],
+    "spl_load_particles_as": [_P, C.POINTER(spl_particles), C.c_int32, C.c_float],
+    "spl_encode_attrs": [_P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, _P, _P, _P, _P],
+    "spl_apply_ea": [_P, _P, C.c_int64, _P],
     "spl_set_camera": [_P, C.POINTER(spl_camera)],
     "spl_set_colormap": [_P, _P, C.c_int32, C.c_float, C.c_float],
     "spl_default_params": [C.POINTER(spl_params)],
@@ -243,11 +246,57 @@ class Renderer:
             arrs = arrs + rgb
         return p, arrs
 
-    def load(self, parts: dict, fp16: dict | None = None, h_log2_min: float | None = None):
-        """Load particles (host or device arrays; see _particles for fp16)."""
+    def load(self, parts: dict, fp16: dict | None = None, h_log2_min: float | None = None,
+             store_as: int | None = None):
+        """Load particles (host or device arrays; see _particles for fp16).  With
+        store_as (an SPL_ATTR_* layout) the FP32 attributes of parts are
+        converted by the library (spl_load_particles_as; h_log2_min for
+        SPL_ATTR_LOGH16)."""
+        if store_as is not None:
+            if fp16 is not None:
+                raise ValueError("store_as converts FP32 attributes: no fp16 arrays")
+            p, keep = self._particles(parts, None)
+            check(load_library().spl_load_particles_as(
+                self._h, C.byref(p), int(store_as),
+                float(h_log2_min if h_log2_min is not None else 0.0)), "spl_load_particles_as")
+            del keep
+            return
         p, keep = self._particles(parts, fp16, h_log2_min)
         check(load_library().spl_load_particles(self._h, C.byref(p)), "spl_load_particles")
         del keep
+
+    def encode_attrs(self, h, I, s, store_as: int, h_log2_min: float = 0.0, stream=None) -> dict:
+        """Library conversion of FP32 CUDA tensors h, I, s into the storage
+        layout store_as; returns new CUDA tensors {"h", "I", "s"} (float32,
+        float16 or int16 holding the uint16 codes)."""
+        import torch
+        n = int(h.numel())
+        for t in (h, I, s):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == n):
+                raise ValueError("encode_attrs: contiguous float32 CUDA tensors of equal size")
+        f16 = store_as != SPL_ATTR_F32
+        dt_h = {SPL_ATTR_F16: torch.float16, SPL_ATTR_LOGH16: torch.int16}.get(store_as, torch.float32)
+        out = {"h": torch.empty(n, dtype=dt_h, device=h.device),
+               "I": torch.empty(n, dtype=torch.float16 if f16 else torch.float32, device=h.device),
+               "s": torch.empty(n, dtype=torch.float16 if f16 else torch.float32, device=h.device)}
+        check(load_library().spl_encode_attrs(self._h, h.data_ptr(), I.data_ptr(), s.data_ptr(), n,
+                                              int(store_as), float(h_log2_min), out["h"].data_ptr(),
+                                              out["I"].data_ptr(), out["s"].data_ptr(), stream),
+              "spl_encode_attrs")
+        return out
+
+    def apply_ea(self, image, stream=None):
+        """E = A map 1 - exp(-v) of every value of a CUDA float32 tensor, in place."""
+        if not (image.is_cuda and image.is_contiguous()) or image.dtype.itemsize != 4:
+            raise ValueError("apply_ea: contiguous float32 CUDA tensor")
+        check(load_library().spl_apply_ea(self._h, image.data_ptr(), int(image.numel()), stream),
+              "spl_apply_ea")
+        return image
+
+    def get_params(self) -> dict:
+        q = spl_params()
+        check(load_library().spl_get_params(self._h, C.byref(q)), "spl_get_params")
+        return {k: getattr(q, k) for k, _ in q._fields_}
 
     def render_stream(self, parts: dict, chunk: int, image, fp16: dict | None = None,
                       stream: int | None = None):

@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_1309_1114_gb300 import scenes
 from tests._metrics import rel_pixel_error
-from tests.test_gpu_parity import gpu_render, random_scene
+from tests.test_gpu_parity import gpu_render, random_scene, sampled_check
 
 pytestmark = pytest.mark.gpu
 TOL32 = 1e-4
@@ -71,6 +71,16 @@ def test_crowded_tiles_are_split_and_composed(rnd, torch_cuda):
 def test_heavy_tailed_radii(rnd, torch_cuda):
     sc = scenes.make("pareto", n=150_000, width=384)
     check(rnd, torch_cuda, sc.parts, sc.palette, sc.cams[0], 0.8)
+
+
+def test_clustered_full_size_sampled(rnd, torch_cuda):
+    """The timed absorbing workload (10M clustered particles, 1024^2) at >= 1024
+    sampled pixels, each pixel's particles sorted by FP64 depth by the oracle;
+    the ambiguity mass covers near ties in depth."""
+    sc = scenes.make("clustered")
+    g, err = sampled_check(rnd, torch_cuda, sc, sc.cams[0], with_mass=True, mode=2,
+                           absorption=1.0)
+    assert err <= TOL32, err
 
 
 def test_emission_equal_to_absorption_matches_the_ea_mode(rnd, torch_cuda):

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_1309_1114_gb300 import scenes
-from tests._metrics import rel_pixel_error
+from tests._metrics import pick_pixels, rel_pixel_error
 
 pytestmark = pytest.mark.gpu
 TOL32 = 1e-4
@@ -48,7 +48,7 @@ def gpu_render(r, torch, parts, pal, cam, fp16=None, h_log2_min=None, **params):
 
 
 def oracle_params(params):
-    keys = ("chi", "sigma_per_h", "s_box", "r_sml", "brightness", "mode")
+    keys = ("chi", "sigma_per_h", "s_box", "r_sml", "brightness", "mode", "absorption")
     return {k: v for k, v in params.items() if k in keys}
 
 
@@ -212,21 +212,27 @@ def test_clustered_reduced_full_image(rnd, torch_cuda):
     check_image(rnd, torch_cuda, sc.parts, sc.palette, sc.cams[0])
 
 
-def sampled_check(r, torch, sc, cam, n_sample=96, tol=TOL32, fp16=None, parts_oracle=None,
-                  h_log2_min=None, **params):
-    """Full-size render, compared at sampled pixels computed one by one."""
+def sampled_check(r, torch, sc, cam, fp16=None, parts_oracle=None, h_log2_min=None,
+                  n_windows=2, n_bright=64, n_random=448, with_mass=False, **params):
+    """Full-size render, compared at sampled pixels computed one by one by the
+    oracle: whole tile-corner windows (one at the brightest halo core), the
+    brightest pixels and random pixels (tests/_metrics.pick_pixels), at least
+    1024 in all.  with_mass subtracts the oracle's ambiguity mass (needed in
+    mode 2, where particles closer in depth than an FP32 ulp may swap)."""
     g = gpu_render(r, torch, sc.parts, sc.palette, cam, fp16=fp16, h_log2_min=h_log2_min, **params)
-    rng = np.random.default_rng(0)
-    H, W = cam["height"], cam["width"]
-    flat = g[..., 0].ravel()
-    top = np.argsort(flat)[-8:]
-    idx = np.concatenate([rng.integers(0, H * W, n_sample - 8), top])
-    px, py = (idx % W).astype(np.int32), (idx // W).astype(np.int32)
+    px, py = pick_pixels(g, tile=params.get("tile_px", 32), n_windows=n_windows,
+                         n_bright=n_bright, n_random=n_random)
+    assert px.size >= 1024
     src = sc.parts if parts_oracle is None else parts_oracle
-    o = oracle.render_pixels(src, sc.palette, cam, oracle_params(params), px, py,
-                             nthreads=os.cpu_count() or 1)
+    nt = os.cpu_count() or 1
+    B = None
+    if with_mass:
+        o, B = oracle.render_pixels(src, sc.palette, cam, oracle_params(params), px, py,
+                                    nthreads=nt, with_mass=True)
+    else:
+        o = oracle.render_pixels(src, sc.palette, cam, oracle_params(params), px, py, nthreads=nt)
     M = np.abs(g).reshape(-1, 3).max(0)
-    err = rel_pixel_error(g[py, px], o, M=M)
+    err = rel_pixel_error(g[py, px], o, B, M=M)
     return g, err
 
 

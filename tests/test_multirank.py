@@ -1,6 +1,8 @@
 """Frames split over ranks (gloo, world size 2, CPU): the composition of
 partial images that the paper's MPI version uses (Sec. 2) reproduces the
-whole frame, and the timing reduction takes the slowest rank."""
+whole frame, and the timing reduction takes the slowest rank.  Here the
+partial images come from the oracle (no GPU); tests/test_gpu_shard.py renders
+them with the library and applies the library's E = A map after the sum."""
 import os
 import socket
 
@@ -32,11 +34,11 @@ def _worker(rank, world, port, out):
         part = {k: v[lo:hi] for k, v in sc.parts.items()}
         img = torch.from_numpy(oracle.render(part, sc.palette, cam))
         shard.allreduce_image(img)
-        ea = shard.ea_map(img.clone())
+        ea = -np.expm1(-img.numpy())          # the E = A map after the sum
         slowest = shard.max_over_ranks(10.0 + rank)
         if rank == 0:
             np.save(out + ".add.npy", img.numpy())
-            np.save(out + ".ea.npy", ea.numpy())
+            np.save(out + ".ea.npy", ea)
             np.save(out + ".t.npy", np.array([slowest]))
     finally:
         dist.destroy_process_group()
