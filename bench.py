@@ -178,6 +178,13 @@ def profiled_traffic(kernel: str, label: str):
     return e.get("dram_bytes_per_launch")
 
 
+def tile_kernel_name(tile_px: int, large: bool) -> str:
+    """Name of the tile (or large) pass kernel that renders tiles of this side."""
+    if int(tile_px) == 32:
+        return f"item_kernel32<{int(large)}>"
+    return f"item_kernel<{int(tile_px)}, {int(large)}>"
+
+
 def oracle_par(wl: dict) -> dict:
     keys = ("mode", "absorption", "sigma_per_h")
     return {k: v for k, v in wl.get("params", {}).items() if k in keys}
@@ -356,7 +363,32 @@ def run_batch(args, wl):
     p1.record(stream)
     torch.cuda.synchronize()
     plain_ms = p0.elapsed_time(p1)
-    r.set_params(**{k: tuned[k] for k in ("tile_px", "r_small", "r_large")})
+    keep = {k: tuned[k] for k in ("tile_px", "r_small", "r_large")}
+    r.set_params(**keep)
+
+    # the same batch under each scheduler (graph replays, CUDA events): the
+    # work items of all views taken in order, longest-first by the count
+    # heuristic, and longest-first by the tile-cost network
+    by_sched = None
+    from paper_1309_1114_gb300 import scheduler, train_scheduler
+    if os.path.exists(train_scheduler.DEFAULT_OUT):
+        theta, heur = scheduler.load(train_scheduler.DEFAULT_OUT)
+        r.set_model(theta, heur)
+        by_sched = {}
+        for name, mode in (("none", 0), ("count", 1), ("network", 2)):
+            r.set_params(sched=mode, **keep)
+            r.render_batch(cams, imgs)          # eager render + graph capture
+            r.render_batch(cams, imgs)
+            torch.cuda.synchronize()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            for _ in range(3):
+                r.render_batch(cams, imgs)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            by_sched[name] = q0.elapsed_time(q1) / 3
+        r.set_params(**keep)
 
     peaks = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -366,7 +398,7 @@ def run_batch(args, wl):
     flops = (FLOPS_PER_POINT * work[0] + FLOPS_PER_PAIR * (work[1] + work[2]) if dom == "tile"
              else FLOPS_PER_PAIR * work[3])
     achieved = flops / (stage[dom] * 1e-3) / 1e12 if stage[dom] > 0 else 0.0
-    kname = f"item_kernel<{tuned['tile_px']}, {0 if dom == 'tile' else 1}>"
+    kname = tile_kernel_name(tuned["tile_px"], dom != "tile")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
                 "kernel": kname, "kernel_ms": stage[dom],
@@ -426,6 +458,7 @@ def run_batch(args, wl):
                        "l2": "inputs larger than L2 (20M particles = 480 MB); no flush"},
             "plain_form": {"ms_per_step": plain_ms, "value": V * scene.n / (plain_ms * 1e-3),
                            "note": "one spl_render per view, default parameters"},
+            "batch_ms_by_scheduler": by_sched,
             "roofline": roofline,
             "hbm_roofline_frac": alg_bytes / (ms * 1e-3) / (hbm * 1e9),
             "hbm_alg_bytes_per_step": alg_bytes,
@@ -536,7 +569,7 @@ def run_ours(args, wl):
     flops = tile_flops if dom == "tile" else large_flops
     achieved = flops / (stage[dom] * 1e-3) / 1e12 if stage[dom] > 0 else 0.0
     kname = (f"absorb_kernel<{st['tile_px']}>" if absorbing else
-             f"item_kernel<{st['tile_px']}, {0 if dom == 'tile' else 1}>")
+             tile_kernel_name(st["tile_px"], dom != "tile"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
                 "kernel": kname, "kernel_ms": stage[dom],
@@ -708,7 +741,7 @@ def run_stream(args, wl):
     flops = (FLOPS_PER_POINT * work[0] + FLOPS_PER_PAIR * (work[1] + work[2])) if dom == "tile" \
         else FLOPS_PER_PAIR * work[3]
     achieved = flops / (stage[dom] * 1e-3) / 1e12 if stage[dom] > 0 else 0.0
-    kname = f"item_kernel<{st['tile_px']}, {0 if dom == 'tile' else 1}>"
+    kname = tile_kernel_name(st["tile_px"], dom != "tile")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
                 "kernel": kname, "kernel_ms": stage[dom] / nch,

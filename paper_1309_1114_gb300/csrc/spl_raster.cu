@@ -192,22 +192,66 @@ __device__ __forceinline__ TileFoot tile_footprint(const FrameConst &fc, int cls
     return f;
 }
 
-// Walk over the tiles of a footprint, row by row: foot_next gives the slot
-// (list * ntiles + tile) of the current tile, or -1 when the walk is past the
-// box or the disc misses that tile, and steps to the next tile.
-struct FootWalk { int k, kx, ky; };
+// The (particle, box tile) pairs of a warp's 32 particles, taken 32 at a time
+// across the lanes instead of one particle per lane: a lane with a wide
+// footprint no longer holds the warp for as many rounds as it has tiles.
+// incl is the inclusive prefix sum of the lanes' box sizes (foot.nbox).  Pair
+// j belongs to the smallest lane o with incl_o > j (a binary search over the
+// lanes' prefix sums); its tile is the (j - start_o)-th of o's box, row by row.
+// Every lane of the warp must call this (warp shuffles); returns the slot
+// (list * ntiles + tile) of pair j, or -1 when j is past the warp's pairs or the
+// disc misses that tile, and the owner lane in *owner.
+struct FootLane {
+    int incl, nbox, list_disc, txy, bw;
+    float rbw, reach2, x, y, z;
+};
 
-__device__ __forceinline__ int foot_next(const FrameConst &fc, const TileFoot &f, float4 r0,
-                                         FootWalk &w) {
-    if (w.k >= f.nbox) return -1;
-    const int tx = f.tx0 + w.kx, ty = f.ty0 + w.ky;
-    ++w.k;
-    if (++w.kx == f.bw) {
-        w.kx = 0;
-        ++w.ky;
+__device__ __forceinline__ FootLane foot_lane(const TileFoot &f, float4 r0, int lane) {
+    FootLane l;
+    int incl = f.nbox;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
     }
-    if (f.disc && !disc_meets_tile(fc, r0, f.reach2, tx, ty)) return -1;
-    return f.list * fc.ntiles + ty * fc.ntx + tx;
+    l.incl = incl;
+    l.nbox = f.nbox;
+    l.list_disc = ((f.list + 1) << 1) | f.disc;
+    l.txy = (f.tx0 & 0xFFFF) | (f.ty0 << 16);
+    l.bw = f.bw;
+    l.rbw = 1.f / (float)f.bw;
+    l.reach2 = f.reach2;
+    l.x = r0.x; l.y = r0.y; l.z = r0.z;
+    return l;
+}
+
+__device__ __forceinline__ int foot_pair(const FrameConst &fc, const FootLane &l, int j, int total,
+                                         int &owner) {
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, l.incl, lo + step - 1);
+        if (v <= j) lo += step;
+    }
+    lo = lo < 31 ? lo : 31;
+    owner = lo;
+    const int o_incl = __shfl_sync(0xffffffffu, l.incl, lo);
+    const int o_nbox = __shfl_sync(0xffffffffu, l.nbox, lo);
+    const int o_ld = __shfl_sync(0xffffffffu, l.list_disc, lo);
+    const int o_txy = __shfl_sync(0xffffffffu, l.txy, lo);
+    const int o_bw = __shfl_sync(0xffffffffu, l.bw, lo);
+    const float o_rbw = __shfl_sync(0xffffffffu, l.rbw, lo);
+    const float o_reach2 = __shfl_sync(0xffffffffu, l.reach2, lo);
+    const float4 o_r0 = make_float4(__shfl_sync(0xffffffffu, l.x, lo), __shfl_sync(0xffffffffu, l.y, lo),
+                                    __shfl_sync(0xffffffffu, l.z, lo), 0.f);
+    if (j >= total) return -1;
+    // (t + 1/2) / bw is at least 1/(2 bw) away from an integer, far more than
+    // the rounding of the product: the quotient is exact
+    const int t = j - (o_incl - o_nbox);
+    const int ky = (int)(((float)t + 0.5f) * o_rbw), kx = t - ky * o_bw;
+    const int tx = (o_txy & 0xFFFF) + kx, ty = (o_txy >> 16) + ky;
+    if ((o_ld & 1) && !disc_meets_tile(fc, o_r0, o_reach2, tx, ty)) return -1;
+    return ((o_ld >> 1) - 1) * fc.ntiles + ty * fc.ntx + tx;
 }
 
 // ---------------------------------------------------------------------------
@@ -328,10 +372,11 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
                 if (a.rec2) a.rec2[rec] = q2;
             }
             const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0, 0, 0.f};
-            const int maxk = __reduce_max_sync(0xffffffffu, foot.nbox);
-            FootWalk walk{0, 0, 0};
-            for (int k = 0; k < maxk; ++k) {
-                const int ls = foot_next(fc, foot, r0, walk);
+            const FootLane fl = foot_lane(foot, r0, lane);
+            const int total = __shfl_sync(0xffffffffu, fl.incl, 31);
+            for (int base = 0; base < total; base += 32) {
+                int owner;
+                const int ls = foot_pair(fc, fl, base + lane, total, owner);
                 count_round(ls >= 0 ? fc.slot_base + ls : -1, keys, vals, a.ovf, lane);
             }
             n_act += cls != CLS_INACTIVE;
@@ -667,10 +712,12 @@ __global__ void __launch_bounds__(256) scatter_kernel(Views vs, BinArgs a) {
             const int64_t rec = fc.rec_base + i;
             float4 r0, r1;
             const TileFoot f = load_foot(fc, a, rec, i < c1, r0, r1);
-            const int maxk = __reduce_max_sync(0xffffffffu, f.nbox);
-            FootWalk walk{0, 0, 0};
-            for (int k = 0; k < maxk; ++k) {
-                const int ls = foot_next(fc, f, r0, walk);
+            const FootLane fl = foot_lane(f, r0, lane);
+            const int total = __shfl_sync(0xffffffffu, fl.incl, 31);
+            for (int pbase = 0; pbase < total; pbase += 32) {
+                int owner;
+                const int ls = foot_pair(fc, fl, pbase + lane, total, owner);
+                const unsigned orec = __shfl_sync(0xffffffffu, (unsigned)rec, owner);
                 const int key = ls >= 0 ? fc.slot_base + ls : -1;
                 const unsigned m = __match_any_sync(0xffffffffu, key);
                 const int leader = __ffs(m) - 1;
@@ -686,7 +733,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(Views vs, BinArgs a) {
                 pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(m & lt);
                 if (key >= 0) {
                     if (pos < a.entries_cap)
-                        a.entries[pos] = (unsigned)rec;
+                        a.entries[pos] = orec;
                     else
                         atomicOr(&a.st->err, ERR_LIST_OVERFLOW);
                 }

@@ -7,8 +7,12 @@
 * longest-first scheduling (count heuristic or network) never changes the
   image;
 * trained on the renderer's own timings, the network predicts held-out item
-  costs better than the count heuristic, and the timing gain of the schedule
-  on a heavy-tailed scene is measured and reported.
+  costs better than the count heuristic;
+* on a heavy-tailed scene the longest work item is measured against its pass
+  (since persistent CTAs take items from a queue, no order of the items can
+  shorten a pass by more than that fraction), and the frame times under each
+  schedule are measured: the asserted result is that neither longest-first
+  schedule beats taking the items in image order (a negative result).
 """
 import os
 
@@ -148,7 +152,7 @@ def test_schedule_does_not_change_the_image(rnd, torch_cuda, sched):
     assert rel_pixel_error(got, o, B) <= 1e-4
 
 
-def test_network_beats_count_heuristic_and_schedule_gain(rnd, torch_cuda):
+def test_network_predicts_better_and_schedule_gain_is_bounded(rnd, torch_cuda):
     from paper_1309_1114_gb300 import scheduler
     # training samples from clustered, precision-like and orbit-like renders
     feats, logcs = [], []
@@ -176,7 +180,11 @@ def test_network_beats_count_heuristic_and_schedule_gain(rnd, torch_cuda):
     print(f"held-out RMSE of log(cycles): network {err_mlp:.3f}, count heuristic {err_cnt:.3f}, "
           f"{f.shape[0]} samples")
     assert err_mlp < err_cnt
-    # the schedule on a heavy-tailed scene: same image, time per frame reported
+    # the schedule on a heavy-tailed scene: what any order of the work items
+    # can gain is bounded by the longest item against its pass (persistent CTAs
+    # take items from a queue, so a pass ends at most one item after the ideal
+    # finish); record every item's SM cycles without a schedule, then time the
+    # frame under each schedule
     sc = scenes.make("pareto", n=4_000_000, width=1024)
     cam = sc.cams[0]
     rnd.load(sc.parts)
@@ -184,6 +192,17 @@ def test_network_beats_count_heuristic_and_schedule_gain(rnd, torch_cuda):
     rnd.set_model(theta, heur)
     rnd.set_camera(cam)
     img = torch_cuda.empty((cam["height"], cam["width"], 3), device="cuda")
+    rnd.set_params()
+    rnd.set_timing(True)
+    for _ in range(3):
+        rnd.render(img)
+    st = rnd.stats()
+    rnd.set_timing(False)
+    pass_ms = st["sum_ms"][2] / max(st["timed_frames"], 1) + st["sum_ms"][3] / max(st["timed_frames"], 1)
+    f, logc = scheduler.collect(rnd, torch_cuda, [cam])
+    cycles = np.exp(logc.cpu().numpy().astype(np.float64))
+    clock_hz = 2.07e9                          # SM clock under load (sm_max_mhz)
+    bound = cycles.max() / (pass_ms * 1e-3 * clock_hz)
     times = {}
     for sched in (0, 1, 2):
         rnd.set_params(sched=sched)
@@ -194,5 +213,14 @@ def test_network_beats_count_heuristic_and_schedule_gain(rnd, torch_cuda):
         st = rnd.stats()
         rnd.set_timing(False)
         times[sched] = st["sum_ms"][5] / max(st["timed_frames"], 1)
-    print("frame ms by scheduler (none, count, network):", times)
+    print(f"longest item / tile + large passes: {bound:.4f} ({cycles.size} items); "
+          f"frame ms by scheduler (none, count, network): {times}")
     rnd.set_params()
+    # the measured result: the better prediction does not turn into a faster
+    # frame -- taking the items in image order keeps neighbouring items on shared
+    # records in L2, the heavy items already start early enough that the tail
+    # the bound allows is not lost, and the network's features cost their own
+    # kernels; neither schedule beats the in-order items by more than timing noise
+    assert 0.0 < bound < 1.0
+    assert times[2] >= times[0] * 0.97
+    assert times[1] >= times[0] * 0.97
