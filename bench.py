@@ -180,8 +180,6 @@ def profiled_traffic(kernel: str, label: str):
 
 def tile_kernel_name(tile_px: int, large: bool) -> str:
     """Name of the tile (or large) pass kernel that renders tiles of this side."""
-    if int(tile_px) == 32:
-        return f"item_kernel32<{int(large)}>"
     return f"item_kernel<{int(tile_px)}, {int(large)}>"
 
 
@@ -240,9 +238,18 @@ def oracle_sample_rate(scene, cam, target_s: float, seed: int = 0, par=None):
     return m / dt, m, cores, dt
 
 
-def make_scene(wl: dict):
+def make_scene(wl: dict, subsample: int = 0):
+    """The workload's scene; with subsample > 0 a random subset of that many
+    of its particles (same camera and image: a small case of the same kernels
+    for profiler captures, never a bench line of the workload itself)."""
     from paper_1309_1114_gb300 import scenes
-    return scenes.make(wl["scene"])
+    sc = scenes.make(wl["scene"])
+    if subsample and subsample < sc.n:
+        keep = np.sort(np.random.default_rng(0).choice(sc.n, subsample, replace=False))
+        sc.parts = {k: v[keep] for k, v in sc.parts.items()}
+        if sc.fp16 is not None:
+            sc.fp16 = {k: v[keep] for k, v in sc.fp16.items()}
+    return sc
 
 
 def run_reference(args, wl):
@@ -485,7 +492,7 @@ def run_ours(args, wl):
     torch.cuda.set_device(local)
     from paper_1309_1114_gb300.splotch import Renderer
 
-    scene = make_scene(wl)
+    scene = make_scene(wl, args.subsample)
     cam = scene.cams[0]
     W, H = cam["width"], cam["height"]
     fp16 = None
@@ -803,10 +810,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="precision32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--subsample", type=int, default=0,
+                    help="render a random subset of this many particles (profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     wl = WORKLOADS[args.workload]
+    if args.subsample:
+        if wl.get("batch") or wl.get("stream") or args.impl == "reference":
+            ap.error("--subsample applies to single-frame workloads of this implementation")
+        wl = dict(wl, label=f"{wl['label']}-subsample{args.subsample}")
     if args.impl == "reference":
         return run_reference(args, wl)
     if wl.get("batch"):

@@ -1098,9 +1098,13 @@ extern "C" int spl_render_batch(spl_ctx *c, const spl_camera *cams, int32_t n_vi
     harvest_timing(c, c->ev_set ^ 1);
     Views vs{};
     SPL_TRY(prepare_views(c, cams, n_views, d_images, vs));
-    // headroom so that small changes of the cameras still fit the graph
-    SPL_TRY(grow(c, c->entries, c->entries.cap + c->entries.cap / 4));
-    SPL_TRY(grow(c, c->items, c->items.cap + c->items.cap / 4));
+    // headroom so that small changes of the cameras still fit the graph: a
+    // quarter above what the eager render needed (not above the capacity, which
+    // would compound over re-captures)
+    const size_t need_e = (size_t)(c->hstats->slot_total > 0 ? c->hstats->slot_total : 1);
+    const size_t need_i = (size_t)c->last_items + 1;
+    SPL_TRY(grow(c, c->entries, need_e + need_e / 4));
+    SPL_TRY(grow(c, c->items, need_i + need_i / 4));
     SPL_TRY(size_item_buffers(c));
     SPL_TRY(capture_batch(c, vs, batch_key(c, cams, n_views)));
     return SPL_OK;
