@@ -60,7 +60,8 @@ WORKLOADS = {
                 "desc": "200k uniform particles, log-normal h, 256x256 RGB FP32"},
     "pareto": {"scene": "pareto", "label": "pareto-400M-4096sq-f32", "sched": True,
                "desc": "400M clustered particles, heavy-tailed smoothing lengths (Pareto alpha 1.5), "
-                       "4096x4096 RGB FP32, work items ordered by the tile-cost network"},
+                       "4096x4096 RGB FP32, work items in tile order (the frame with items "
+                       "ordered by the count heuristic and by the tile-cost network timed beside it)"},
     "stream": {"scene": "precision", "label": "stream-100M-2048sq-f32-chunks12.5M", "stream": 12_500_000,
                "desc": "100M clustered particles kept in page-locked host memory, FP32 attributes, "
                        "streamed through the GPU in 8 chunks of 12.5M (copy of chunk k+1 overlaps "
@@ -70,6 +71,8 @@ WORKLOADS = {
                       "resolutions cycling 512^2/1024^2/2048^2, one batched graph-replayed render"},
 }
 METRIC = "particles/s per GB300 at stated error vs FP64 oracle; % of HBM roofline"
+E2E_STREAM_MIN = 16_000_000   # end-to-end through the out-of-core call from this size on
+E2E_CHUNKS = 8
 FLOPS_PER_PAIR = 7      # separable weight product (1 mul) + 3 multiply-adds
 FLOPS_PER_POINT = 3     # 3 adds
 # absorption: tau (2 mul), 1 - exp(-tau) (1 transcendental + 1), T (1 - e^-tau)
@@ -153,19 +156,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_hash() -> str:
+# the source files a kernel is compiled from (its counters stay valid while
+# these are unchanged)
+KERNEL_SOURCES = {
+    "item_kernel": ("spl_tile.cu", "spl_geom.cuh", "spl_internal.cuh"),
+    "absorb_kernel": ("spl_tile.cu", "spl_geom.cuh", "spl_internal.cuh"),
+}
+
+
+def source_hash(files=None) -> str:
+    """Hash of the kernel sources (the named files of csrc/, else all of them)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1309_1114_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    names = sorted(files) if files else sorted(
+        n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh")))
+    for name in names:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, label: str):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the
-    current kernel sources (else None)."""
+def profiled_entry(kernel: str, label: str):
+    """The committed ncu figures of this kernel on this workload
+    (profiles/traffic.json), if its sources are unchanged since (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -173,9 +187,21 @@ def profiled_traffic(kernel: str, label: str):
     except Exception:
         return None
     e = d.get(f"{kernel}@{label}")
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(KERNEL_SOURCES.get(kernel.split("<")[0])):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
+
+
+def profiled_traffic(kernel: str, label: str):
+    """DRAM bytes per launch from the committed ncu figures (else None)."""
+    e = profiled_entry(kernel, label)
+    return e.get("dram_bytes_per_launch") if e else None
+
+
+def profiled_limiter(kernel: str, label: str):
+    """The pipe that bounds the kernel in the committed ncu figures (else None)."""
+    e = profiled_entry(kernel, label)
+    return e.get("limiter") if e else None
 
 
 def tile_kernel_name(tile_px: int, large: bool) -> str:
@@ -408,6 +434,7 @@ def run_batch(args, wl):
     kname = tile_kernel_name(tuned["tile_px"], dom != "tile")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
+                "limiter": profiled_limiter(kname, wl["label"]),
                 "kernel": kname, "kernel_ms": stage[dom],
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                               f"{sm_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
@@ -517,18 +544,20 @@ def run_ours(args, wl):
     r.set_colormap(scene.palette)
     r.set_camera(cam)
     r.set_params(**wl.get("params", {}))
+    # the timed frame takes the work items in tile order (measured fastest);
+    # with "sched" the frame under the count heuristic and the tile-cost
+    # network is timed beside it
     sched_mode = 0
     model_info = None
+    have_model = False
     if wl.get("sched"):
         from paper_1309_1114_gb300 import scheduler, train_scheduler
-        sched_mode = 1
         if os.path.exists(train_scheduler.DEFAULT_OUT):
             theta, heur = scheduler.load(train_scheduler.DEFAULT_OUT)
             r.set_model(theta, heur)
-            sched_mode = 2
+            have_model = True
             with open(train_scheduler.DEFAULT_OUT) as fh:
                 model_info = {k: v for k, v in json.load(fh).items() if k not in ("theta", "heur")}
-        r.set_params(sched=sched_mode, **wl.get("params", {}))
     img = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
     work = r.count_work()
 
@@ -579,6 +608,7 @@ def run_ours(args, wl):
              tile_kernel_name(st["tile_px"], dom != "tile"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
+                "limiter": profiled_limiter(kname, wl["label"]),
                 "kernel": kname, "kernel_ms": stage[dom],
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                               f"{sm_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
@@ -590,7 +620,7 @@ def run_ours(args, wl):
         # the same frame with each scheduler (CUDA-event frame times, 5 frames each)
         schedulers = {}
         for name, mode in (("none", 0), ("count", 1), ("network", 2)):
-            if mode == 2 and sched_mode != 2:
+            if mode == 2 and not have_model:
                 continue
             r.set_params(sched=mode)
             r.render(img)
@@ -600,7 +630,7 @@ def run_ours(args, wl):
             sst = r.stats()
             r.set_timing(False)
             schedulers[name] = sst["sum_ms"][5] / max(sst["timed_frames"], 1)
-        r.set_params(sched=sched_mode)
+        r.set_params(sched=sched_mode, **wl.get("params", {}))
     bytes_per_particle = {None: 24, "all": 18, "is": 20, "logh": 18}[wl.get("fp16")]
     alg_bytes = scene.n * bytes_per_particle + 12 * W * H
     hbm = float(peaks.get("hbm_gbs", 6771.1))
@@ -618,14 +648,26 @@ def run_ours(args, wl):
     xyz = {k: host_parts[k] for k in ("x", "y", "z")}
     attrs = {k: host_parts[k] for k in ("h", "I", "s")}
     host_np = host_img.numpy()
+    f32_parts = dict(xyz, **{k: attrs[k] for k in attrs if fp16 is None or k not in fp16})
+    half_parts = None if fp16 is None else {k: attrs[k] for k in fp16}
+    # large sets: the out-of-core call, whose chunk uploads overlap the render
+    # of the previous chunk (the call a caller with host arrays makes); small
+    # ones: upload, then render into host memory
+    stream_chunk = -(-scene.n // E2E_CHUNKS) if scene.n >= E2E_STREAM_MIN else 0
+    img_e2e = torch.empty_like(img) if stream_chunk else None
+
+    def e2e_step():
+        if stream_chunk:
+            r.render_stream(f32_parts, stream_chunk, img_e2e, half_parts, h_log2_min=h_log2_min)
+            host_img.copy_(img_e2e)
+        else:
+            r.load(f32_parts, half_parts, h_log2_min)
+            r.render_host(host_np)
+
+    e2e_step()                        # untimed: the chunk buffers are allocated once
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        if fp16 is None:
-            r.load(dict(xyz, **attrs))
-        else:
-            r.load(dict(xyz, **{k: attrs[k] for k in attrs if k not in fp16}),
-                   {k: attrs[k] for k in fp16}, h_log2_min)
-        r.render_host(host_np)
+        e2e_step()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if ws > 1:
         t = torch.tensor([e2e_s], device="cuda")
@@ -633,7 +675,11 @@ def run_ours(args, wl):
         e2e_s = float(t.item())
     e2e = {"value": ws * scene.n / e2e_s, "unit": "particles/s",
            "h2d_bytes_per_step": scene.n * bytes_per_particle, "d2h_bytes_per_step": 12 * W * H,
-           "ms_per_step": 1e3 * e2e_s}
+           "ms_per_step": 1e3 * e2e_s,
+           "api": (f"spl_render_stream from page-locked host arrays, {E2E_CHUNKS} chunks of "
+                   f"{stream_chunk} particles, image read back" if stream_chunk else
+                   "spl_load_particles from page-locked host arrays + spl_render_host")}
+    del img_e2e
 
     cpu = None
     error = None
@@ -751,6 +797,7 @@ def run_stream(args, wl):
     kname = tile_kernel_name(st["tile_px"], dom != "tile")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": profiled_traffic(kname, wl["label"]),
+                "limiter": profiled_limiter(kname, wl["label"]),
                 "kernel": kname, "kernel_ms": stage[dom] / nch,
                 "note": f"the dominant kernel runs once per chunk ({nch} per step); achieved = "
                         "algorithmic flops of the whole set / summed launch time",

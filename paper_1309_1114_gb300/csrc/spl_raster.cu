@@ -283,16 +283,19 @@ __device__ __forceinline__ int hash_slot(const int *keys, int key, bool insert) 
     return -1;
 }
 
-// Count the slots of one round (k-th tile of every lane's footprint); a key
+// Count the slots of one round (one (particle, tile) pair per lane); a key
 // with no room in the table is counted in ovf (placed through the cursors).
-__device__ __forceinline__ void count_round(int key, int *keys, int *vals, int *govf, int lane) {
-    const unsigned m = __match_any_sync(0xffffffffu, key);
-    if (key >= 0 && lane == __ffs(m) - 1) {
+// Each lane adds its own pair: the counts need no return value, and combining
+// the warp's equal keys first (a match mask) cost more than it saved
+// (clustered 10M / 1024^2 raster 0.425 -> 0.388 ms, 30M / 2048^2 1.462 ->
+// 1.244 ms).  The scatter, which needs each entry's rank, keeps the match.
+__device__ __forceinline__ void count_round(int key, int *keys, int *vals, int *govf) {
+    if (key >= 0) {
         const int slot = hash_slot(keys, key, true);
         if (slot >= 0)
-            atomicAdd(&vals[slot], __popc(m));
+            atomicAdd(&vals[slot], 1);
         else
-            atomicAdd(&govf[key], __popc(m));
+            atomicAdd(&govf[key], 1);
     }
 }
 
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
             for (int base = 0; base < total; base += 32) {
                 int owner;
                 const int ls = foot_pair(fc, fl, base + lane, total, owner);
-                count_round(ls >= 0 ? fc.slot_base + ls : -1, keys, vals, a.ovf, lane);
+                count_round(ls >= 0 ? fc.slot_base + ls : -1, keys, vals, a.ovf);
             }
             n_act += cls != CLS_INACTIVE;
             n_pt += cls == CLS_POINT;

@@ -299,10 +299,11 @@ class Renderer:
         return {k: getattr(q, k) for k, _ in q._fields_}
 
     def render_stream(self, parts: dict, chunk: int, image, fp16: dict | None = None,
-                      stream: int | None = None):
+                      stream: int | None = None, h_log2_min: float | None = None):
         """Out-of-core render of host particle arrays (page-locked for overlap)
-        in chunks of `chunk` particles into the device image."""
-        p, keep = self._particles(parts, fp16)
+        in chunks of `chunk` particles into the device image (fp16 and
+        h_log2_min as in load)."""
+        p, keep = self._particles(parts, fp16, h_log2_min)
         check(load_library().spl_render_stream(self._h, C.byref(p), int(chunk), image.data_ptr(),
                                                stream), "spl_render_stream")
         del keep
