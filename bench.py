@@ -159,8 +159,8 @@ class ClockSampler:
 # the source files a kernel is compiled from (its counters stay valid while
 # these are unchanged)
 KERNEL_SOURCES = {
-    "item_kernel": ("spl_tile.cu", "spl_geom.cuh", "spl_internal.cuh"),
-    "absorb_kernel": ("spl_tile.cu", "spl_geom.cuh", "spl_internal.cuh"),
+    "item_kernel": ("spl_tile.cu", "spl_tile.cuh", "spl_geom.cuh", "spl_internal.cuh"),
+    "absorb_kernel": ("spl_absorb.cu", "spl_tile.cuh", "spl_geom.cuh", "spl_internal.cuh"),
 }
 
 
@@ -243,13 +243,14 @@ def stated_error(scene, cam, g, par, tol, n_windows=1, n_bright=64, n_random=448
             "oracle_s": time.perf_counter() - t0}
 
 
-def oracle_sample_rate(scene, cam, target_s: float, seed: int = 0, par=None):
-    """Time the FP64 oracle (all host cores; one for the depth-ordered absorption
-    mode, which the oracle runs serially) on a random sample of the scene, sized
-    to take about target_s seconds.  Returns (particles/s, sample, cores, secs)."""
+def oracle_sample_rate(scene, cam, target_s: float, seed: int = 0, par=None, threads=None):
+    """Time the FP64 oracle (all host cores unless threads is given; one for the
+    depth-ordered absorption mode, which the oracle runs serially) on a random
+    sample of the scene, sized to take about target_s seconds.  Returns
+    (particles/s, sample, cores, secs)."""
     import oracle
     par = dict(par or {})
-    cores = 1 if par.get("mode") == 2 else (os.cpu_count() or 1)
+    cores = 1 if par.get("mode") == 2 else (threads or os.cpu_count() or 1)
     rng = np.random.default_rng(seed)
     m = min(scene.n, 20000)
     for _ in range(4):
@@ -693,6 +694,11 @@ def run_ours(args, wl):
         cpu = {"value": rate, "unit": "particles/s", "cores": cores, "kind": "oracle",
                "sample": f"{m} particles drawn at random from the workload, full {W}x{H} image, "
                          f"FP64, OpenMP over {cores} threads, {secs:.1f} s"}
+        if cores > 1:
+            r1, m1, _, s1 = oracle_sample_rate(scene, cam, 3.0, seed=1, par=oracle_par(wl),
+                                               threads=1)
+            cpu["single_thread"] = {"value": r1, "unit": "particles/s",
+                                    "sample": f"{m1} particles at random, one thread, {s1:.1f} s"}
 
     if rank == 0:
         line = {
