@@ -231,8 +231,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) absorb_kernel(Views vs, TileA
             const int cnt = (int)(le - base < S::P ? le - base : S::P);
             if (tid < cnt) {
                 const unsigned id = a.entries[base + tid];
-                st0[tid] = a.rec0[id];
-                st1[tid] = a.rec1[id];
+                const Rec rc = a.recs[id];
+                st0[tid] = rc.r0;
+                st1[tid] = rc.r1;
                 st2[tid] = a.rec2[id];
             }
             if (tid < kTileThreads / 32) band_mask[tid] = 0u;

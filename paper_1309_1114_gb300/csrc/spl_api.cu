@@ -88,7 +88,7 @@ struct spl_ctx {
     bool have_cam = false;
     spl_params par{};
     // scratch
-    DevBuf<float4> rec0, rec1;
+    DevBuf<Rec> recs;
     // absorption mode: (A, depth key) per record, the depth-order sort, and the
     // (C, T) partials of split tiles
     DevBuf<float2> rec2;
@@ -274,7 +274,7 @@ extern "C" int spl_destroy(spl_ctx *c) {
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     c->pal.release();
-    c->rec0.release(); c->rec1.release();
+    c->recs.release();
     c->rec2.release(); c->pkeys.release(); c->ptmp.release(); c->ekeys.release();
     c->etmp.release(); c->rank.release(); c->sort_hist.release(); c->partial.release();
     c->counts.release(); c->offsets.release(); c->cursor.release();
@@ -615,8 +615,7 @@ static int prepare_views(spl_ctx *c, const spl_camera *cams, int V, float *const
     }
     if ((int64_t)V * src_n(c) > (int64_t)0xFFFFFFFFLL) return SPL_EINVAL;   // record ids are 32-bit
     const size_t recs = (size_t)V * (size_t)src_n(c);
-    SPL_TRY(grow(c, c->rec0, recs ? recs : 1));
-    SPL_TRY(grow(c, c->rec1, recs ? recs : 1));
+    SPL_TRY(grow(c, c->recs, recs ? recs : 1));
     if (c->par.mode == SPL_MODE_ABSORB) {
         SPL_TRY(grow(c, c->rec2, recs ? recs : 1));
         SPL_TRY(grow(c, c->pkeys, recs ? recs : 1));
@@ -681,7 +680,7 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
         ra.h_log2_min = c->h_log2_min;
     }
     ra.pal = c->pal.p;
-    ra.rec0 = c->rec0.p; ra.rec1 = c->rec1.p;
+    ra.recs = c->recs.p;
     ra.rec2 = c->par.mode == SPL_MODE_ABSORB ? c->rec2.p : nullptr;
     ra.counts = c->counts.p;
     ra.ovf = c->ovf.p;
@@ -691,7 +690,7 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
     launch_raster(vs, ra, c->streaming ? c->chunk_attr : c->attr_type, s);
     record_event(c, 1, s);
     BinArgs ba{};
-    ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
+    ba.recs = c->recs.p;
     ba.large_ids = c->large_ids.p;
     ba.counts = c->counts.p;
     ba.ovf = c->ovf.p;
@@ -711,7 +710,7 @@ static void enqueue_binning(spl_ctx *c, const Views &vs, cudaStream_t s) {
 static void enqueue_lists(spl_ctx *c, const Views &vs, cudaStream_t s) {
     if (!c->accumulate) launch_zero_images(vs, c->d_images.p, c->sms, s);
     BinArgs ba{};
-    ba.rec0 = c->rec0.p; ba.rec1 = c->rec1.p;
+    ba.recs = c->recs.p;
     ba.large_ids = c->large_ids.p;
     ba.counts = c->counts.p;
     ba.ovf = c->ovf.p;
@@ -729,7 +728,7 @@ static void enqueue_lists(spl_ctx *c, const Views &vs, cudaStream_t s) {
 // Stage 3: schedule the work items, the tile and large passes, the epilogue.
 static void enqueue_passes(spl_ctx *c, const Views &vs, bool large_pass, cudaStream_t s) {
     TileArgs ta{};
-    ta.rec0 = c->rec0.p; ta.rec1 = c->rec1.p;
+    ta.recs = c->recs.p;
     ta.offsets = c->offsets.p;
     ta.entries = c->entries.p;
     ta.items = c->items.p;
@@ -757,7 +756,7 @@ static void enqueue_passes(spl_ctx *c, const Views &vs, bool large_pass, cudaStr
     if (c->par.mode == SPL_MODE_ABSORB) {
         // one view: every entry sits in the medium slots [L_MEDIUM * nt, (L_MEDIUM + 1) * nt]
         const int nt = c->h_fcs[0].ntiles;
-        launch_depth_order(c->rec1.p, c->rec2.p, vs.n, c->entries.p, c->offsets.p + L_MEDIUM * nt,
+        launch_depth_order(c->recs.p, c->rec2.p, vs.n, c->entries.p, c->offsets.p + L_MEDIUM * nt,
                            nt, (long long)c->hstats->slot_total, c->pkeys.p, c->ptmp.p,
                            c->ekeys.p, c->etmp.p, c->rank.p, c->sort_hist.p, c->sms, s);
         ta.rec2 = c->rec2.p;
@@ -1274,7 +1273,7 @@ extern "C" int spl_get_records(spl_ctx *c, int64_t n, double *xs, double *ys, fl
                                int32_t *cls) {
     if (!c || n < 0 || n > c->n) return SPL_EINVAL;
     if (n == 0) return SPL_OK;
-    if ((size_t)n > c->rec0.cap || (size_t)n > c->rec1.cap) return SPL_ESTATE;
+    if ((size_t)n > c->recs.cap) return SPL_ESTATE;
     DeviceGuard g(c->device);
     float4 *h0 = new (std::nothrow) float4[n];
     float4 *h1 = new (std::nothrow) float4[n];
@@ -1284,8 +1283,13 @@ extern "C" int spl_get_records(spl_ctx *c, int64_t n, double *xs, double *ys, fl
         return SPL_ENOMEM;
     }
     int rc = cuda_status(cudaStreamSynchronize(c->stream));
-    if (rc == SPL_OK) rc = cuda_status(cudaMemcpy(h0, c->rec0.p, n * sizeof(float4), cudaMemcpyDeviceToHost));
-    if (rc == SPL_OK) rc = cuda_status(cudaMemcpy(h1, c->rec1.p, n * sizeof(float4), cudaMemcpyDeviceToHost));
+    // the two halves of the 32-byte records into two host arrays (pitched copies)
+    if (rc == SPL_OK)
+        rc = cuda_status(cudaMemcpy2D(h0, sizeof(float4), &c->recs.p->r0, sizeof(Rec), sizeof(float4),
+                                      (size_t)n, cudaMemcpyDeviceToHost));
+    if (rc == SPL_OK)
+        rc = cuda_status(cudaMemcpy2D(h1, sizeof(float4), &c->recs.p->r1, sizeof(Rec), sizeof(float4),
+                                      (size_t)n, cudaMemcpyDeviceToHost));
     if (rc == SPL_OK) {
         const double rs2 = (double)(float)(c->par.r_sml * c->par.r_sml);
         const double rm2 = (double)(float)(c->par.r_small * c->par.r_small);
@@ -1331,7 +1335,7 @@ extern "C" int spl_count_work(spl_ctx *c, int64_t out[4]) {
         c->timing = false;
         enqueue_binning(c, vs, s);
         c->timing = timing;
-        launch_count_work(c->h_fcs[0], c->rec0.p, c->rec1.p, c->n, work.p, c->sms, s);
+        launch_count_work(c->h_fcs[0], c->recs.p, c->n, work.p, c->sms, s);
         unsigned long long h[4] = {0, 0, 0, 0};
         rc = cuda_status(cudaGetLastError());
         if (rc == SPL_OK) rc = cuda_status(cudaMemcpyAsync(h, work.p, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -1360,9 +1364,8 @@ constexpr int kNaMaxItems = 32768;
 constexpr size_t na_round(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kNaStats = 0;
 constexpr size_t kNaPal = kNaStats + na_round(sizeof(DevStats));
-constexpr size_t kNaRec0 = kNaPal + na_round(sizeof(float) * 3 * kMaxPalette);
-constexpr size_t kNaRec1 = kNaRec0 + na_round(sizeof(float4) * kNaMaxParticles);
-constexpr size_t kNaLarge = kNaRec1 + na_round(sizeof(float4) * kNaMaxParticles);
+constexpr size_t kNaRecs = kNaPal + na_round(sizeof(float) * 3 * kMaxPalette);
+constexpr size_t kNaLarge = kNaRecs + na_round(sizeof(Rec) * kNaMaxParticles);
 constexpr size_t kNaCounts = kNaLarge + na_round(sizeof(unsigned) * kNaMaxParticles);
 constexpr size_t kNaOffsets = kNaCounts + na_round(sizeof(int) * NLIST * kNaMaxTiles);
 constexpr size_t kNaCursor = kNaOffsets + na_round(sizeof(long long) * (NLIST * kNaMaxTiles + 1));
@@ -1451,8 +1454,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     SPL_TRY(na_scratch(device, &base));
     DevStats *dst = reinterpret_cast<DevStats *>(base + kNaStats);
     float *pal = reinterpret_cast<float *>(base + kNaPal);
-    float4 *rec0 = reinterpret_cast<float4 *>(base + kNaRec0);
-    float4 *rec1 = reinterpret_cast<float4 *>(base + kNaRec1);
+    Rec *recs = reinterpret_cast<Rec *>(base + kNaRecs);
     unsigned *large_ids = reinterpret_cast<unsigned *>(base + kNaLarge);
     int *counts = reinterpret_cast<int *>(base + kNaCounts);
     long long *offsets = reinterpret_cast<long long *>(base + kNaOffsets);
@@ -1495,7 +1497,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     ra.cr = p->cr; ra.cg = p->cg; ra.cb = p->cb;
     ra.h_log2_min = p->h_log2_min;
     ra.pal = pal;
-    ra.rec0 = rec0; ra.rec1 = rec1;
+    ra.recs = recs;
     ra.counts = counts;
     ra.ovf = ovf;
     ra.ctab = ctab;
@@ -1503,7 +1505,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     ra.st = dst;
     launch_raster(vs, ra, p->attr_type, s);
     BinArgs ba{};
-    ba.rec0 = rec0; ba.rec1 = rec1;
+    ba.recs = recs;
     ba.large_ids = large_ids;
     ba.counts = counts;
     ba.ovf = ovf;
@@ -1534,7 +1536,7 @@ extern "C" int spl_render_noalloc(const spl_particles *p, const spl_camera *cam,
     launch_scatter(vs, ba, sms, s);
     launch_fill_items(vs, offsets, item_offsets, items, kNaMaxItems, dst, s);
     TileArgs ta{};
-    ta.rec0 = rec0; ta.rec1 = rec1;
+    ta.recs = recs;
     ta.offsets = offsets;
     ta.entries = entries;
     ta.items = items;

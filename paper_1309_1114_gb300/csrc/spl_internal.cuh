@@ -115,6 +115,14 @@ __host__ __device__ constexpr int64_t ctab_entries(int64_t n, int nviews) {
            (nviews > 0 ? nviews : 1) * kHash;
 }
 
+// One rasterised particle: r0 = (packed pixel xi, yi; sub-pixel xf, yf;
+// 1 / (sigma^2 ln 2)), r1 = (r^2; e_R, e_G, e_B).  The two halves sit in one
+// 32-byte record, so that a gather through a tile list reads one sector.
+struct Rec {
+    float4 r0, r1;
+};
+static_assert(sizeof(Rec) == 32, "32-byte records");
+
 struct RasterArgs {
     int64_t n;
     const float *x, *y, *z;
@@ -122,7 +130,7 @@ struct RasterArgs {
     const float *pal;          // npal * 3
     const float *cr, *cg, *cb; // optional per-particle colour components (replace the palette)
     float h_log2_min;          // ATTR 3: h = 2^(h_log2_min + code / 4096)
-    float4 *rec0, *rec1;       // nviews * n records
+    Rec *recs;                 // nviews * n records
     float2 *rec2;              // absorption mode: (A, depth key) per record, else null
     int *counts;               // list slots of all views: entries counted through the CTA tables
     int *ovf;                  // list slots: entries placed through the cursors (see BinArgs)
@@ -137,7 +145,7 @@ struct RasterArgs {
 // one warp group at a time through cursor[k] = offsets[k] + counts[k]: those
 // of keys that found no room in a CTA table, and the large list (ovf[k]).
 struct BinArgs {
-    const float4 *rec0, *rec1;
+    const Rec *recs;
     const unsigned *large_ids;
     long long *cursor;         // list slots, starts at offsets + counts
     int *counts;
@@ -150,7 +158,7 @@ struct BinArgs {
 };
 
 struct TileArgs {
-    const float4 *rec0, *rec1;
+    const Rec *recs;
     const long long *offsets;  // list slots of all views, + 1 (64-bit list positions)
     const unsigned *entries;
     const WorkItem *items;
@@ -197,7 +205,7 @@ void launch_absorb_pass(const Views &v, const TileArgs &a, const int *item_offse
                         cudaStream_t s);
 int radix_blocks(int64_t n);
 int64_t radix_scratch_ints(int64_t n);
-void launch_depth_order(const float4 *rec1, const float2 *rec2, int64_t n, unsigned *entries,
+void launch_depth_order(const Rec *recs, const float2 *rec2, int64_t n, unsigned *entries,
                         const long long *off, int ntiles, long long total, unsigned long long *pkeys,
                         unsigned long long *ptmp, unsigned long long *ekeys,
                         unsigned long long *etmp, unsigned *rank, int *hist, int sms,
@@ -213,7 +221,7 @@ void launch_slot_cursor(int m, const int *counts, const long long *offsets, long
 // image pointers are read from device memory, so a graph can replay them).
 void launch_zero_images(const Views &v, float *const *images, int sms, cudaStream_t s);
 void launch_epilogue_views(const Views &v, float *const *images, int sms, cudaStream_t s);
-void launch_count_work(const FrameConst &fc, const float4 *rec0, const float4 *rec1, int64_t n,
+void launch_count_work(const FrameConst &fc, const Rec *recs, int64_t n,
                        unsigned long long *work, int sms, cudaStream_t s);
 
 // Scheduling of the work items (spl_sched.cu): per-item features, predicted

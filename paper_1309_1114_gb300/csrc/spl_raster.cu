@@ -370,8 +370,7 @@ __global__ void __launch_bounds__(256, 4) raster_kernel(Views vs, RasterArgs a) 
                 cls = raster_one(fc, spal, a.x[i], a.y[i], a.z[i], load_h<ATTR>(a.h, i, a.h_log2_min),
                                  load_attr<ATTR != 0>(a.I, i), load_attr<ATTR != 0>(a.s, i),
                                  RGB ? crgb : nullptr, r0, r1, q2);
-                a.rec0[rec] = r0;
-                a.rec1[rec] = r1;
+                a.recs[rec] = Rec{r0, r1};
                 if (a.rec2) a.rec2[rec] = q2;
             }
             const TileFoot foot = valid ? tile_footprint(fc, cls, r0, r1) : TileFoot{-1, 0, 0, 1, 0, 0, 0.f};
@@ -453,8 +452,8 @@ __global__ void __launch_bounds__(256) large_tiles_kernel(Views vs, BinArgs a) {
     for (unsigned w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nl; w += warps) {
         const unsigned rec = a.large_ids[w];
         const FrameConst &fc = vs.fcs[(int)(rec / (unsigned long long)vs.n)];
-        const float4 r0 = a.rec0[rec];
-        const float4 r1 = a.rec1[rec];
+        const Rec rc = a.recs[rec];
+        const float4 r0 = rc.r0, r1 = rc.r1;
         PixBox b;
         if (!splat_box(fc, r0, r1.x, b)) continue;
         const int tx0 = b.i0 >> fc.tile_shift, ty0 = b.j0 >> fc.tile_shift;
@@ -674,10 +673,11 @@ __device__ __forceinline__ TileFoot load_foot(const FrameConst &fc, const BinArg
     r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     r1 = make_float4(-1.f, 0.f, 0.f, 0.f);
     if (!valid) return TileFoot{-1, 0, 0, 1, 0, 0, 0.f};
-    r1 = a.rec1[rec];
+    const Rec rc = a.recs[rec];
+    r1 = rc.r1;
     const int cls = record_class(fc, r1.x);
     if (cls == CLS_INACTIVE || cls == CLS_LARGE) return TileFoot{-1, 0, 0, 1, 0, 0, 0.f};
-    r0 = a.rec0[rec];
+    r0 = rc.r0;
     return tile_footprint(fc, cls, r0, r1);
 }
 
@@ -760,16 +760,15 @@ void launch_scatter(const Views &vs, const BinArgs &a, int sms, cudaStream_t s) 
 // Diagnostic: exact count of covered (particle, pixel) pairs per class, using
 // the same FP32 clip test as the render passes.  Not part of a render.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) count_work_kernel(FrameConst fc, const float4 *rec0,
-                                                         const float4 *rec1, int64_t n,
+__global__ void __launch_bounds__(256) count_work_kernel(FrameConst fc, const Rec *recs, int64_t n,
                                                          unsigned long long *work) {
     unsigned long long acc[4] = {0, 0, 0, 0};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float4 r1 = rec1[i];
+        const float4 r1 = recs[i].r1;
         const int cls = record_class(fc, r1.x);
         if (cls == CLS_INACTIVE) continue;
-        const float4 r0 = rec0[i];
+        const float4 r0 = recs[i].r0;
         const int xi = unpack_xi(r0.x), yi = unpack_yi(r0.x);
         if (cls == CLS_POINT) {
             acc[0] += (xi >= 0 && yi >= 0 && xi < fc.width && yi < fc.height);
@@ -796,12 +795,12 @@ __global__ void __launch_bounds__(256) count_work_kernel(FrameConst fc, const fl
     }
 }
 
-void launch_count_work(const FrameConst &fc, const float4 *rec0, const float4 *rec1, int64_t n,
+void launch_count_work(const FrameConst &fc, const Rec *recs, int64_t n,
                        unsigned long long *work, int sms, cudaStream_t s) {
     if (n <= 0) return;
     int64_t blocks = (n + 255) / 256;
     blocks = blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8;
-    count_work_kernel<<<(unsigned)blocks, 256, 0, s>>>(fc, rec0, rec1, n, work);
+    count_work_kernel<<<(unsigned)blocks, 256, 0, s>>>(fc, recs, n, work);
     ++g_launches;
 }
 

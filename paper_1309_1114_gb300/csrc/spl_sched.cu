@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) item_features_kernel(Views vs, TileArgs a
             const float wgt = (float)stride;
             for (long long k = b + lane * stride; k < e; k += 32 * stride) {
                 const unsigned rec = a.entries[k];
-                const float4 r0 = a.rec0[rec], r1 = a.rec1[rec];
+                const Rec rc = a.recs[rec];
+                const float4 r0 = rc.r0, r1 = rc.r1;
                 const int bin = radius_bin(r1.x);
                 float area = 1.f;
                 if (record_class(fc, r1.x) != CLS_POINT) {

@@ -210,12 +210,12 @@ unsigned long long *launch_radix_sort(unsigned long long *keys, unsigned long lo
 // Particle keys: (float bits of the depth key) << 32 | index; the depth key is
 // positive for every active particle (z_c > z_near > 0), so its bits order as
 // the value.  Inactive or non-absorbing records go last.
-__global__ void depth_keys_kernel(const float4 *rec1, const float2 *rec2, int64_t n,
+__global__ void depth_keys_kernel(const Rec *recs, const float2 *rec2, int64_t n,
                                   unsigned long long *keys) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float2 q = rec2[i];
-        const bool live = rec1[i].x >= 0.f && q.x > 0.f;
+        const bool live = recs[i].r1.x >= 0.f && q.x > 0.f;
         const unsigned hi = live ? __float_as_uint(q.y) : 0xFFFFFFFFu;
         keys[i] = ((unsigned long long)hi << 32) | (unsigned long long)(unsigned)i;
     }
@@ -268,13 +268,13 @@ static int bits_for(unsigned long long v) {
 // total, off[ntiles] - off[0], known after the binning synchronisation).
 // pkeys/ptmp: n particle keys each; ekeys/etmp: total entry keys each;
 // rank: n; hist: radix_scratch_ints(max(n, total)) ints.
-void launch_depth_order(const float4 *rec1, const float2 *rec2, int64_t n, unsigned *entries,
+void launch_depth_order(const Rec *recs, const float2 *rec2, int64_t n, unsigned *entries,
                         const long long *off, int ntiles, long long total, unsigned long long *pkeys,
                         unsigned long long *ptmp, unsigned long long *ekeys,
                         unsigned long long *etmp, unsigned *rank, int *hist, int sms,
                         cudaStream_t s) {
     if (n <= 0 || total <= 0) return;
-    depth_keys_kernel<<<sms * 8, 256, 0, s>>>(rec1, rec2, n, pkeys);
+    depth_keys_kernel<<<sms * 8, 256, 0, s>>>(recs, rec2, n, pkeys);
     ++g_launches;
     int shifts[8], np = 0;
     const int idb = bits_for((unsigned long long)(n - 1));

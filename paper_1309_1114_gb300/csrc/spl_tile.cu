@@ -377,14 +377,16 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
         if (lb2 < le2) {
             if (lb2 + tid < le2 && tid < S::P) {
                 const unsigned id = a.entries[lb2 + tid];
-                st0[tid] = a.rec0[id];
-                st1[tid] = a.rec1[id];
+                const Rec rc = a.recs[id];
+                st0[tid] = rc.r0;
+                st1[tid] = rc.r1;
             }
             if (tid < NW) band_mask[0][tid] = 0u;
             if (lb2 + S::P + tid < le2 && tid < S::P) {
                 const unsigned id = a.entries[lb2 + S::P + tid];
-                n0 = a.rec0[id];
-                n1 = a.rec1[id];
+                const Rec rc = a.recs[id];
+                n0 = rc.r0;
+                n1 = rc.r1;
             }
             __syncthreads();
         }
@@ -403,8 +405,9 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
                 }
                 if (base + 2 * S::P + tid < le2) {
                     const unsigned id = a.entries[base + 2 * S::P + tid];
-                    n0 = a.rec0[id];
-                    n1 = a.rec1[id];
+                    const Rec rc = a.recs[id];
+                    n0 = rc.r0;
+                    n1 = rc.r1;
                 }
             }
             if (tid < NW) band_mask[buf ^ 1][tid] = 0u;
@@ -433,8 +436,9 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
             const int cnt = (int)(le0 - base < kTileThreads ? le0 - base : kTileThreads);
             if (tid < cnt) {
                 const unsigned id = a.entries[base + tid];
-                st0[tid] = a.rec0[id];
-                st1[tid] = a.rec1[id];
+                const Rec rc = a.recs[id];
+                st0[tid] = rc.r0;
+                st1[tid] = rc.r1;
             }
             __syncthreads();
             warp_points<T>(a, st0 + warp * 32, st1 + warp * 32, cnt - warp * 32, x0, y0, sacc, lane);
@@ -444,7 +448,8 @@ __global__ void __launch_bounds__(kTileThreads, min_ctas<T>()) item_kernel(Views
 #pragma unroll 1
         for (long long k = lb1 + tid; k < le1; k += kTileThreads) {
             const unsigned id = a.entries[k];
-            thread_small<T>(fc, a.rec0[id], a.rec1[id], x0, y0, sacc);
+            const Rec rc = a.recs[id];
+            thread_small<T>(fc, rc.r0, rc.r1, x0, y0, sacc);
         }
         if (le1 > lb1) __syncthreads();
         // write: shared part + registers, stored (only item of its tile; added
