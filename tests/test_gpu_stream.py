@@ -36,7 +36,8 @@ def rnd(torch_cuda):
     r.close()
 
 
-def streamed(r, torch, parts, pal, cam, chunk, fp16=None, pinned=False, **params):
+def streamed(r, torch, parts, pal, cam, chunk, fp16=None, pinned=False, h_log2_min=None,
+             **params):
     r.set_colormap(pal)
     r.set_params(**params)
     r.set_camera(cam)
@@ -45,7 +46,7 @@ def streamed(r, torch, parts, pal, cam, chunk, fp16=None, pinned=False, **params
         if fp16 is not None:
             fp16 = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in fp16.items()}
     img = torch.full((cam["height"], cam["width"], 3), float("nan"), device="cuda")
-    r.render_stream(parts, chunk, img, fp16)
+    r.render_stream(parts, chunk, img, fp16, h_log2_min=h_log2_min)
     torch.cuda.synchronize()
     return img.cpu().numpy().astype(np.float64)
 
@@ -88,11 +89,15 @@ def test_stream_with_large_particles_split_tiles_and_ea_map(rnd, torch_cuda):
 
 
 def test_stream_fp16_attributes(rnd, torch_cuda):
+    from tests._codes import log16_h
     sc = scenes.make("precision", n=300_000, width=384)
     cam = sc.cams[0]
-    for fp16 in (sc.fp16, {k: sc.fp16[k] for k in ("I", "s")}):
-        base = gpu_render(rnd, torch_cuda, sc.parts, sc.palette, cam, fp16=fp16)
-        got = streamed(rnd, torch_cuda, sc.parts, sc.palette, cam, 99_999, fp16=fp16, pinned=True)
+    half = {k: sc.fp16[k] for k in ("I", "s")}
+    logh = dict(half, h=log16_h(sc.parts["h"], -14.0))
+    for fp16, lmin in ((sc.fp16, None), (half, None), (logh, -14.0)):
+        base = gpu_render(rnd, torch_cuda, sc.parts, sc.palette, cam, fp16=fp16, h_log2_min=lmin)
+        got = streamed(rnd, torch_cuda, sc.parts, sc.palette, cam, 99_999, fp16=fp16, pinned=True,
+                       h_log2_min=lmin)
         assert same(got, base)
 
 
