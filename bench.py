@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -164,16 +165,24 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and blank space: the code a kernel is
+    compiled from (an edited comment leaves its counters valid)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_hash(files=None) -> str:
-    """Hash of the kernel sources (the named files of csrc/, else all of them)."""
+    """Hash of the kernel sources' code (the named files of csrc/, else all of them)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1309_1114_gb300", "csrc")
     names = sorted(files) if files else sorted(
         n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh")))
     for name in names:
-        with open(os.path.join(csrc, name), "rb") as f:
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
             h.update(name.encode())
-            h.update(f.read())
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

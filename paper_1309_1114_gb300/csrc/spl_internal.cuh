@@ -3,9 +3,9 @@
 // Data layout in HBM (one frame):
 //   particles   SoA: x, y, z (FP32) and h, I, s (FP32 or binary16), owned by the
 //               context, read once per frame by the rasteriser.
-//   records     two float4 arrays indexed by particle id (32 B per particle):
-//                 rec0 = { packed (xi, yi) as two int16, xf, yf, kq }
-//                 rec1 = { r^2 (negative when inactive), e_R, e_G, e_B }
+//   records     one 32-byte Rec per particle id (and view):
+//                 r0 = { packed (xi, yi) as two int16, xf, yf, kq }
+//                 r1 = { r^2 (negative when inactive), e_R, e_G, e_B }
 //               where x_s = xi + xf with xf in [0, 1) (the integer part keeps
 //               the sub-pixel position exact to ~1e-7 px in FP32) and
 //               kq = log2(e) / sigma_s^2, so exp(-d^2/sigma^2) = 2^(-kq d^2).

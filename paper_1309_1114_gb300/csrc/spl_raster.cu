@@ -257,10 +257,9 @@ __device__ __forceinline__ int foot_pair(const FrameConst &fc, const FootLane &l
 // ---------------------------------------------------------------------------
 // Per-CTA aggregation of list slots.  A clustered particle set puts 1e5-1e6
 // entries into single tiles; one global atomic per entry then serialises in
-// L2.  Each CTA takes a contiguous chunk of particles, combines the entries
-// of a warp that share a slot (match), and accumulates the rest in a small
-// shared-memory hash table (open addressing, key = list * ntiles + tile), so
-// that a hot slot receives one global atomic per CTA.  A key that finds no
+// L2.  Each CTA takes a contiguous chunk of particles and accumulates its
+// entries in a small shared-memory hash table (open addressing, key = list *
+// ntiles + tile), so that a hot slot receives one global atomic per CTA.  A key that finds no
 // free place within kProbe probes falls back to global atomics; the table is
 // never emptied while a CTA runs, so that choice is the same for every
 // occurrence of the key within the CTA.
