@@ -165,8 +165,19 @@ __host__ __device__ constexpr size_t absorb_smem_bytes() {
            (2 * sizeof(float4) + sizeof(float2)) * S::P;              // staged records
 }
 
+// CTAs per SM.  The pass is latency-bound (each pixel's transmittance is a
+// chain across its list), so occupancy pays: at T = 32, 2 -> 4 -> 6 CTAs per
+// SM (106 -> 62 -> 40 registers, 8 bytes spilled at 40) took the clustered
+// 10M / 1024^2 pass from 15.2 to 11.3 to 10.7 ms.  At T = 64 a lane's 16
+// pixels need the registers of 2 CTAs per SM; at T = 16, 5 fit without spills.
+#ifndef SPL_ABS32
+#define SPL_ABS32 6
+#endif
 template <int T>
-__global__ void __launch_bounds__(kTileThreads, 2) absorb_kernel(Views vs, TileArgs a) {
+constexpr int absorb_ctas() { return T == 64 ? 2 : (T == 32 ? SPL_ABS32 : 5); }
+
+template <int T>
+__global__ void __launch_bounds__(kTileThreads, absorb_ctas<T>()) absorb_kernel(Views vs, TileArgs a) {
     using S = Shape<T>;
     extern __shared__ float4 smem_raw[];
     float2 (*swx)[S::WXS] = reinterpret_cast<float2 (*)[S::WXS]>(smem_raw);
@@ -369,7 +380,7 @@ template <int T>
 static void launch_absorb_t(const Views &vs, const TileArgs &a, const int *item_offsets, int sms,
                             cudaStream_t s) {
     constexpr size_t bytes = absorb_smem_bytes<T>();
-    absorb_kernel<T><<<sms * 2, kTileThreads, bytes, s>>>(vs, a);
+    absorb_kernel<T><<<sms * absorb_ctas<T>(), kTileThreads, bytes, s>>>(vs, a);
     ++g_launches;
     const int grid = vs.total_tiles < sms * 8 ? vs.total_tiles : sms * 8;
     if (grid > 0) {
