@@ -282,7 +282,9 @@ void launch_depth_order(const Rec *recs, const float2 *rec2, int64_t n, unsigned
     ++g_launches;
     int shifts[8], np = 0;
     const int idb = bits_for((unsigned long long)(n - 1));
-    for (int sh = 0; sh < idb; sh += 8) shifts[np++] = sh;
+    // the keys start in index order and every pass is stable, so sorting by
+    // the depth bits alone leaves equal depths in index order: the index bits
+    // need no passes of their own
     for (int sh = 32; sh < 64; sh += 8) shifts[np++] = sh;
     unsigned long long *ps = launch_radix_sort(pkeys, ptmp, n, shifts, np, hist, s);
     rank_kernel<<<sms * 8, 256, 0, s>>>(ps, n, rank);
