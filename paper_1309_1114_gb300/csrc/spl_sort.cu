@@ -64,11 +64,17 @@ __global__ void __launch_bounds__(kSortThreads, 5) radix_scatter_kernel(const un
     const int64_t w0 = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortItems;
     unsigned long long key[kSortItems];
     int rnk[kSortItems];
+    // all of the warp's keys are loaded before the ranking rounds, whose warp
+    // barriers would otherwise serialise the loads' latencies
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t i = w0 + r * 32 + lane;
+        key[r] = i < n ? in[i] : 0ull;
+    }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t i = w0 + r * 32 + lane;
         const bool valid = i < n;
-        key[r] = valid ? in[i] : 0ull;
         const int d = valid ? (int)digit_of(key[r], shift) : -1;
         const unsigned m = __match_any_sync(0xffffffffu, d);
         int before = 0;
