@@ -628,36 +628,47 @@ __device__ __forceinline__ void put_item(WorkItem *items, int cap, int pos, Work
         atomicOr(&st->err, ERR_LIST_OVERFLOW);
 }
 
+// One warp per tile: the lanes write the tile's segments side by side (a
+// crowded tile has hundreds), in the same order as one thread would.
 __global__ void fill_items_kernel(Views vs, const long long *off, const int *ioff, WorkItem *items,
                                   int cap, DevStats *st) {
     const int T = vs.total_tiles;
     const int seg[NLIST] = {kSegPoint, kSegSmall, kSegMedium, kSegLarge};
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < T; g += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < T; g += warps) {
         const int v = view_of_tile(vs.fcs, vs.nviews, g);
         const FrameConst &fc = vs.fcs[v];
         const int t = g - fc.tile_base, nt = fc.ntiles, sb = fc.slot_base;
         int w = ioff[g];
         const int nw = ioff[g + 1] - w;
         if (nw == 1) {
-            put_item(items, cap, w, {g, (v << 8) | kAllLists, 0, 0}, st);
+            if (lane == 0) put_item(items, cap, w, {g, (v << 8) | kAllLists, 0, 0}, st);
         } else if (nw > 1) {
             for (int l = 0; l < L_LARGE; ++l) {
                 const long long b = off[sb + l * nt + t], e = off[sb + l * nt + t + 1];
-                for (long long k = b; k < e; k += seg[l])
-                    put_item(items, cap, w++, {g, (v << 8) | l, k, k + seg[l] < e ? k + seg[l] : e}, st);
+                const int ns = (int)((e - b + seg[l] - 1) / seg[l]);
+                for (int k = lane; k < ns; k += 32) {
+                    const long long kb = b + (long long)k * seg[l];
+                    put_item(items, cap, w + k, {g, (v << 8) | l, kb, kb + seg[l] < e ? kb + seg[l] : e}, st);
+                }
+                w += ns;
             }
         }
-        int wl = ioff[T + g];
+        const int wl = ioff[T + g];
         const long long b = off[sb + L_LARGE * nt + t], e = off[sb + L_LARGE * nt + t + 1];
-        for (long long k = b; k < e; k += kSegLarge)
-            put_item(items, cap, wl++,
-                     {g, (v << 8) | L_LARGE, k, k + kSegLarge < e ? k + kSegLarge : e}, st);
+        const int ns = (int)((e - b + kSegLarge - 1) / kSegLarge);
+        for (int k = lane; k < ns; k += 32) {
+            const long long kb = b + (long long)k * kSegLarge;
+            put_item(items, cap, wl + k,
+                     {g, (v << 8) | L_LARGE, kb, kb + kSegLarge < e ? kb + kSegLarge : e}, st);
+        }
     }
 }
 
 void launch_fill_items(const Views &vs, const long long *offsets, const int *item_offsets,
                        WorkItem *items, int items_cap, DevStats *st, cudaStream_t s) {
-    const int blocks = (vs.total_tiles + 255) / 256;
+    const int blocks = (vs.total_tiles + 7) / 8;     // 8 warps of 256 threads, a warp per tile
     fill_items_kernel<<<blocks, 256, 0, s>>>(vs, offsets, item_offsets, items, items_cap, st);
     ++g_launches;
 }
