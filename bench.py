@@ -13,15 +13,18 @@ no collective on the data path); timing is the max over ranks.
 
 `--impl reference` times the FP64 CPU oracle (the correctness reference) on
 the host cores, each step a random sample of the same workload.
+`--subsample M` renders a random M-particle subset of the workload (same camera
+and image): a small case of the same kernels for profiler captures, labelled
+as such in the line.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
-import re
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
