@@ -170,11 +170,8 @@ __host__ __device__ constexpr size_t absorb_smem_bytes() {
 // SM (106 -> 62 -> 40 registers, 8 bytes spilled at 40) took the clustered
 // 10M / 1024^2 pass from 15.2 to 11.3 to 10.7 ms.  At T = 64 a lane's 16
 // pixels need the registers of 2 CTAs per SM; at T = 16, 5 fit without spills.
-#ifndef SPL_ABS32
-#define SPL_ABS32 6
-#endif
 template <int T>
-constexpr int absorb_ctas() { return T == 64 ? 2 : (T == 32 ? SPL_ABS32 : 5); }
+constexpr int absorb_ctas() { return T == 64 ? 2 : (T == 32 ? 6 : 5); }
 
 template <int T>
 __global__ void __launch_bounds__(kTileThreads, absorb_ctas<T>()) absorb_kernel(Views vs, TileArgs a) {
