@@ -70,3 +70,31 @@ def test_stated_error_of_the_oracle_image_is_zero_and_a_planted_error_is_seen(be
     g[j, i, 0] *= 1.01
     e = bench.stated_error(sc, cam, g, {}, 1e-4)
     assert 0.009 < e["max_rel"] < 0.011 and not e["within_tol"]
+
+
+def test_committed_counter_entries_are_well_formed(bench):
+    """Every entry of profiles/traffic.json names its kernel and workload, its
+    positive DRAM bytes per launch, the source files of its kernel, and the
+    capture command (one pass of the plain program, then ncu with the clocks
+    left alone)."""
+    import json
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        d = json.load(f)
+    labels = {w["label"] for w in bench.WORKLOADS.values()}
+    assert d
+    for key, e in d.items():
+        kernel, _, label = key.partition("@")
+        assert label in labels, key
+        base = kernel.split("<")[0]
+        assert base in bench.KERNEL_SOURCES, key
+        assert e["dram_bytes_per_launch"] > 0
+        assert e["sources"] == ", ".join(bench.KERNEL_SOURCES[base])
+        assert len(e["source_hash"]) == 16
+        cmd = e["command"]
+        assert cmd.startswith("python bench.py") and " && ncu " in cmd
+        assert "--clock-control none" in cmd
+        if "captured_bytes_per_launch" in e:     # a subsample capture scaled to the full launch
+            assert "--subsample" in cmd and e["dram_bytes_per_launch"] > e["captured_bytes_per_launch"]
+        lim = e.get("limiter")
+        if lim:
+            assert os.path.exists(os.path.join(ROOT, lim["profile"]))
